@@ -1,0 +1,153 @@
+/*
+ * gsr.h - C ABI of libgsr, a single-GPU (B300, sm_103a) implementation of the
+ * hot path of the Gaia AVU-GSR solver (arXiv 2503.22863):
+ *   aprod 1  y += A x      (Sec. 2.1, Eq. 2)
+ *   aprod 2  x += A^T y    (Sec. 2.1, Eq. 3)
+ *   preconditioned LSQR on A x = b (Sec. 2, Eq. 1; solver steps 2-5 of Sec. 2),
+ *   the Paige-Saunders algorithm cited in Sec. 1.
+ *
+ * Matrix (Sec. 2): n_rows observation equations, each with at most 24
+ * coefficients: 5 astrometric, 12 attitude (3 axes x 4 consecutive spline
+ * knots), 6 instrumental and 1 global. Host input is "dense by row":
+ *   vals      double  [n_rows][24]  slot order: astro 0..4 | att axis0 knot
+ *                                   +0..3, axis1 +0..3, axis2 +0..3 | instr 0..5 | glob
+ *   astro_off int64   [n_rows]      5*star(i); rows sorted by star (non-decreasing)
+ *   att_off   int64   [n_rows]      5*n_stars + s_i, 0 <= s_i <= n_knots-4; the
+ *                                   three axes use s_i at offsets 0, n_knots, 2*n_knots
+ *   instr     int32   [n_rows][6]   distinct instrumental indices in [0, n_instr)
+ * Column layout of x (N_unk = 5*n_stars + 3*n_knots + n_instr + n_glob):
+ *   [astro 5*n_stars | attitude 3*n_knots | instrumental n_instr | global n_glob]
+ * The slot and column conventions are this library's reading: the paper fixes
+ * only the per-row counts.
+ *
+ * Conventions for every call:
+ *   - Vector arguments marked "device" are caller-owned device pointers on the
+ *     system's device (for example torch tensors); the library never frees them.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - Every call returns a gsr_status; nothing aborts or prints.
+ *     gsr_strerror() gives the text. After GSR_E_CUDA the system should be
+ *     destroyed.
+ *   - Arithmetic: products and sums run as pairs of FP32 numbers with
+ *     error-free transformations (about 48 significant bits, within 1e-13 of
+ *     FP64 relative to |A||x|); vectors, norms and LSQR scalars are FP64.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsr_system gsr_system; /* opaque, library-owned */
+
+typedef enum {
+  GSR_OK = 0,
+  GSR_E_ARG = 1,         /* null pointer, negative size, bad option */
+  GSR_E_INDEX = 2,       /* an offset or index outside its block */
+  GSR_E_UNSORTED = 3,    /* rows not sorted by star */
+  GSR_E_NONFINITE = 4,   /* NaN or Inf in the matrix or right-hand side */
+  GSR_E_OOM = 5,         /* device allocation failed */
+  GSR_E_CUDA = 6,        /* a CUDA runtime call failed */
+  GSR_E_TIMEOUT = 7,     /* a bounded device-side wait ran out */
+  GSR_E_UNSUPPORTED = 8  /* sizes beyond this build's limits (see gsr_create) */
+} gsr_status;
+
+/* Which stored copy of the matrix values an aprod call reads. */
+enum { GSR_VALUES_F64 = 0, GSR_VALUES_F32 = 1 };
+/* Storage of the matrix values. F32_PLUS_F64 keeps an FP32 copy (half the
+ * bytes, used by the mixed-precision solve) beside the full-precision one. */
+enum { GSR_STORE_F64 = 0, GSR_STORE_F32_PLUS_F64 = 1 };
+/* Column preconditioner (Sec. 2, solver steps 2 and 5). */
+enum { GSR_PRECOND_NONE = 0, GSR_PRECOND_COLNORM = 1, GSR_PRECOND_USER = 2 };
+/* LSQR precision mode. */
+enum { GSR_PREC_F64 = 0, GSR_PREC_MIXED = 1 };
+
+typedef struct {
+  int64_t n_rows, n_stars, n_knots, n_instr;
+  int32_t n_glob;  /* 0 or 1 */
+  int32_t storage; /* GSR_STORE_* */
+} gsr_dims;
+
+/*
+ * Create a system on `device` from host arrays (layout above). The arrays are
+ * read during the call only; the library keeps its own device copies in a
+ * tiled, coalesced layout plus a copy of the attitude coefficients sorted by
+ * start knot, and computes the column norms ||A_:,j||_2. Synchronous.
+ * Validation: GSR_E_ARG (null/negative, n_knots < 4, n_instr < 6, n_glob not
+ * 0/1), GSR_E_INDEX (astro_off not 5*star in range, s_i outside [0, K-4],
+ * instr outside [0, n_instr) or repeated in a row), GSR_E_UNSORTED (astro_off
+ * decreasing), GSR_E_NONFINITE (NaN/Inf value), GSR_E_UNSUPPORTED (n_rows or
+ * N_unk >= 2^31, or n_instr > 28672: the instrumental histogram of aprod 2
+ * lives in one block's shared memory), GSR_E_OOM.
+ * On success *out owns everything; release it with gsr_destroy().
+ */
+int gsr_create(const gsr_dims* dims, const double* vals, const int64_t* astro_off,
+               const int64_t* att_off, const int32_t* instr, int device, void* stream,
+               gsr_system** out);
+
+void gsr_destroy(gsr_system* sys);
+const char* gsr_strerror(int status);
+int64_t gsr_n_unknowns(const gsr_system* sys);
+int64_t gsr_n_rows(const gsr_system* sys);
+
+/* Eq. 2 (aprod 1): y[n_rows] += A x[N_unk]. x, y device; x is not modified. */
+int gsr_aprod1(gsr_system* sys, const double* x, double* y, void* stream);
+/* Eq. 3 (aprod 2): x[N_unk] += A^T y[n_rows]. x, y device. */
+int gsr_aprod2(gsr_system* sys, const double* y, double* x, void* stream);
+/* As above on a chosen copy of the values (GSR_VALUES_F32 needs
+ * GSR_STORE_F32_PLUS_F64; with it the products use the FP32-rounded A). */
+int gsr_aprod1_values(gsr_system* sys, int which_values, const double* x, double* y,
+                      void* stream);
+int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double* x,
+                      void* stream);
+
+/* Column norms c_j = ||A_:,j||_2 (FP64 copy of the values) into c[N_unk], device. */
+int gsr_column_norms(gsr_system* sys, double* c, void* stream);
+
+typedef struct {
+  double atol, btol, conlim; /* Paige-Saunders stopping tolerances (conlim 0 = off) */
+  int64_t itnlim;            /* iteration limit (istop = 7 when reached) */
+  int32_t precond;           /* GSR_PRECOND_*; USER takes `scale` */
+  int32_t precision;         /* GSR_PREC_F64 or GSR_PREC_MIXED */
+  const double* scale;       /* device [N_unk], d_j > 0, for GSR_PRECOND_USER */
+  double* var;               /* optional device [N_unk]: variance estimate out */
+  const double* x_ref;       /* optional device [N_unk]: per-iteration error reference */
+  double* err_hist;          /* optional host [itnlim]: ||x_k - x_ref|| / ||x_ref|| */
+  double* rnorm_hist;        /* optional host [itnlim]: estimate of ||b - A x_k|| */
+  int32_t mixed_switch_itn;  /* MIXED: iterations of the FP32-values phase (0 = auto) */
+  int32_t profile;           /* 1: time aprod 1 / aprod 2 / vector kernels with CUDA
+                                events recorded inside the iteration graph */
+} gsr_lsqr_opts;
+
+typedef struct {
+  int32_t istop;   /* 0 x=0 solves; 1,2 converged; 3 cond limit; 4,5 machine precision;
+                      6 cond at machine precision; 7 itnlim reached (not an error) */
+  int32_t phase2_itn; /* MIXED: iterations of the FP64 correction phase */
+  int64_t itn;
+  double rnorm, arnorm, anorm, acond, xnorm;
+  int64_t n_launches;    /* kernels this call launched (including no-op tail launches) */
+  int64_t n_timed_itn;   /* iterations covered by the timings below (profile = 1) */
+  double t_aprod1_ms, t_aprod2_ms, t_vector_ms; /* summed device time per kernel group */
+} gsr_lsqr_result;
+
+/* Fill opts with defaults: atol = btol = 1e-12, conlim = 1e12, itnlim = 0
+ * (meaning 20*N_unk), COLNORM, F64, no outputs. */
+void gsr_lsqr_default_opts(gsr_lsqr_opts* opts);
+
+/*
+ * Solve min ||A x - b||_2 by LSQR on A D (D from opts.precond), returning the
+ * de-preconditioned x = D z (Sec. 2, solver steps 2-5). b [n_rows] and x
+ * [N_unk] are device pointers. Blocks until the result is final (one host
+ * read of the stopping flag every few iterations). Reaching itnlim returns
+ * GSR_OK with istop = 7.
+ */
+int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_opts* opts,
+                   gsr_lsqr_result* res, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

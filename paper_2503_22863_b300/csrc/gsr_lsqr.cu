@@ -1,0 +1,555 @@
+// Preconditioned LSQR (Paige & Saunders 1982, the solver of Sec. 2 / Sec. 2.1)
+// on the column-scaled operator A D, with every scalar kept on the device.
+//
+// One iteration is five stream-ordered launches:
+//   1. aprod 1:  u~ <- A (D v) - (alpha/beta) u~   and ||u~||^2        (Eq. 2)
+//   2. z <- 0;   aprod 2: z <- A^T u~  (star-ordered + knot-ordered parts) (Eq. 3)
+//   3. vec_a:    v~ <- D z / beta - beta v, ||v~||^2; the last block runs the
+//                plane rotation (rho, c, s, theta, rhobar, phi, phibar)
+//   4. vec_b:    x <- x + (phi/rho) w, w <- v~/alpha - (theta/rho) w, the
+//                float-pair copy D v for the next aprod 1, ||x||, ||d_k||^2;
+//                the last block evaluates the stopping tests
+// u is kept unnormalised (u = u~/beta) so that no pass over the rows is spent
+// on normalising it. Iterations are captured once into a CUDA graph and
+// replayed in chunks; all kernels return immediately once the stop flag is
+// set, so the host reads the flag only once per chunk.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+enum Scal {
+  S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_DDNORM, S_BNORM, S_XNORM,
+  S_RHO, S_C, S_S, S_THETA, S_PHI, S_T1, S_T2, S_RNORM, S_ARNORM, S_ACOND,
+  S_ATOL, S_BTOL, S_CTOL, S_ITN, S_ITNLIM, S_ISTOP, S_DONE,
+  S_UNORM2, S_VNORM2, S_COEF_U, S_ERR2, S_XREF2, S_RED3, S_RED3B, S_RED3C,
+  S_COUNT
+};
+
+constexpr int RED_BLOCKS = 148 * 8;  // grid of the vector kernels
+
+__device__ __forceinline__ double block_sum3(double& a, double& b, double& c, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+  c = warp_sum_d(c);
+  __syncthreads();
+  if (lane == 0) {
+    sh[wid] = a;
+    sh[32 + wid] = b;
+    sh[64 + wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < nw ? sh[lane] : 0.0;
+    b = lane < nw ? sh[32 + lane] : 0.0;
+    c = lane < nw ? sh[64 + lane] : 0.0;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    c = warp_sum_d(c);
+  }
+  return a;
+}
+
+// Deterministic grid reduction of three sums; returns true in the last block
+// (thread 0 then holds the totals in a, b, c).
+__device__ bool grid_sum3(double& a, double& b, double& c, double* part, unsigned int* counter) {
+  __shared__ double sh[96];
+  __shared__ int is_last;
+  block_sum3(a, b, c, sh);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double x = 0.0, y = 0.0, z = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+    x += __ldcg(part + 3 * i);
+    y += __ldcg(part + 3 * i + 1);
+    z += __ldcg(part + 3 * i + 2);
+  }
+  block_sum3(x, y, z, sh);
+  if (threadIdx.x == 0) {
+    a = x;
+    b = y;
+    c = z;
+    *counter = 0u;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Start: u~ = b (and its knot-order copy), ||b||^2.
+// ---------------------------------------------------------------------------
+__global__ void k_init_u(Layout L, const double* __restrict__ b, double* __restrict__ u,
+                         double* __restrict__ u_knot, double* scal, double* part,
+                         unsigned int* counter) {
+  const int32_t* pos = reinterpret_cast<const int32_t*>(L.att_pos);
+  double s2 = 0.0, z0 = 0.0, z1 = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[r];
+    u[r] = v;
+    u_knot[pos[r]] = v;
+    s2 = __fma_rn(v, v, s2);
+  }
+  if (grid_sum3(s2, z0, z1, part, counter) && threadIdx.x == 0) scal[S_UNORM2] = s2;
+}
+
+// ---------------------------------------------------------------------------
+// vec_a: v~ = d z / beta - beta v (v absent on the first call); ||v~||^2;
+// then (last block) the scalar step.
+// ---------------------------------------------------------------------------
+__global__ void k_vec_a(int64_t n, const double* __restrict__ d, const double* __restrict__ z,
+                        double* __restrict__ v, double* scal, double* part, unsigned int* counter,
+                        int first) {
+  if (scal[S_DONE] != 0.0) return;
+  const double beta = sqrt(scal[S_UNORM2]);
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  double s2 = 0.0, z0 = 0.0, z1 = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double t = d[j] * z[j] * ib;
+    if (!first) t = __fma_rn(-beta, v[j], t);
+    v[j] = t;
+    s2 = __fma_rn(t, t, s2);
+  }
+  if (!grid_sum3(s2, z0, z1, part, counter) || threadIdx.x != 0) return;
+  const double alpha = sqrt(s2);
+  if (first) {
+    scal[S_BETA] = beta;
+    scal[S_BNORM] = beta;
+    scal[S_ALPHA] = alpha;
+    scal[S_RHOBAR] = alpha;
+    scal[S_PHIBAR] = beta;
+    scal[S_RNORM] = beta;
+    scal[S_ARNORM] = alpha * beta;
+    scal[S_COEF_U] = beta > 0.0 ? -alpha / beta : 0.0;
+    if (alpha * beta == 0.0) {  // b = 0 or A^T b = 0: x = 0 is the solution
+      scal[S_ISTOP] = 0.0;
+      scal[S_DONE] = 1.0;
+    }
+    return;
+  }
+  const double alpha_old = scal[S_ALPHA];
+  scal[S_ANORM2] += alpha_old * alpha_old + beta * beta;
+  const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
+  const double rho = sqrt(rhobar * rhobar + beta * beta);
+  const double c = rhobar / rho, s = beta / rho;
+  const double theta = s * alpha;
+  scal[S_RHO] = rho;
+  scal[S_C] = c;
+  scal[S_S] = s;
+  scal[S_THETA] = theta;
+  scal[S_RHOBAR] = -c * alpha;
+  scal[S_PHI] = c * phibar;
+  scal[S_PHIBAR] = s * phibar;
+  scal[S_T1] = c * phibar / rho;
+  scal[S_T2] = -theta / rho;
+  scal[S_BETA] = beta;
+  scal[S_ALPHA] = alpha;
+  scal[S_COEF_U] = beta > 0.0 ? -alpha / beta : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// vec_b: normalise v, update x and w, write D v as float pairs, ||x||,
+// ||d_k||^2 and the variance; then (last block) the stopping tests.
+// ---------------------------------------------------------------------------
+__global__ void k_vec_b(int64_t n, const double* __restrict__ d, double* __restrict__ v,
+                        double* __restrict__ w, double* __restrict__ xz,
+                        float2* __restrict__ v_ff, double* __restrict__ var,
+                        const double* __restrict__ x_ref, double* scal, double* part,
+                        unsigned int* counter, int first, double* err_hist, double* rnorm_hist) {
+  if (scal[S_DONE] != 0.0) return;
+  const double alpha = scal[S_ALPHA];
+  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  const double rho = first ? 1.0 : scal[S_RHO];
+  const double irho = 1.0 / rho;
+  const double t1 = first ? 0.0 : scal[S_T1], t2 = first ? 0.0 : scal[S_T2];
+  double dk2 = 0.0, x2 = 0.0, e2 = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double vn = v[j] * ia;
+    const double dj = d[j];
+    double xv;
+    if (first) {
+      w[j] = vn;
+      xz[j] = 0.0;
+      xv = 0.0;
+    } else {
+      const double wj = w[j];
+      const double dk = wj * irho;
+      dk2 = __fma_rn(dk, dk, dk2);
+      if (var) var[j] = __fma_rn(dk, dk, var[j]);
+      const double xn = __fma_rn(t1, wj, xz[j]);
+      xz[j] = xn;
+      w[j] = __fma_rn(t2, wj, vn);
+      xv = dj * xn;
+      x2 = __fma_rn(xv, xv, x2);
+    }
+    v[j] = vn;
+    const ff f = ff_from_double(dj * vn);
+    v_ff[j] = make_float2(f.h, f.l);
+    if (x_ref) {
+      const double e = xv - x_ref[j];
+      e2 = __fma_rn(e, e, e2);
+    }
+  }
+  if (!grid_sum3(dk2, x2, e2, part, counter) || threadIdx.x != 0) return;
+  if (first) return;
+  const double itn = scal[S_ITN] + 1.0;
+  scal[S_ITN] = itn;
+  const double ddnorm = scal[S_DDNORM] + dk2;
+  scal[S_DDNORM] = ddnorm;
+  const double anorm = sqrt(scal[S_ANORM2]);
+  const double acond = anorm * sqrt(ddnorm);
+  const double rnorm = scal[S_PHIBAR];
+  const double arnorm = alpha * fabs(scal[S_C]) * rnorm;
+  const double xnorm = sqrt(x2);
+  const double bnorm = scal[S_BNORM];
+  scal[S_ACOND] = acond;
+  scal[S_RNORM] = rnorm;
+  scal[S_ARNORM] = arnorm;
+  scal[S_XNORM] = xnorm;
+  const int64_t k = (int64_t)itn - 1;
+  if (err_hist) {
+    const double xr2 = scal[S_XREF2];
+    err_hist[k] = xr2 > 0.0 ? sqrt(e2 / xr2) : sqrt(e2);
+  }
+  if (rnorm_hist) rnorm_hist[k] = rnorm;
+  const double atol = scal[S_ATOL], btol = scal[S_BTOL], ctol = scal[S_CTOL];
+  const double test1 = rnorm / bnorm;
+  const double test2 = (anorm * rnorm > 0.0) ? arnorm / (anorm * rnorm) : 0.0;
+  const double test3 = 1.0 / acond;
+  const double t1n = test1 / (1.0 + anorm * xnorm / bnorm);
+  const double rtol = btol + atol * anorm * xnorm / bnorm;
+  int istop = 0;
+  if (itn >= scal[S_ITNLIM]) istop = 7;
+  if (1.0 + test3 <= 1.0) istop = 6;
+  if (1.0 + test2 <= 1.0) istop = 5;
+  if (1.0 + t1n <= 1.0) istop = 4;
+  if (test3 <= ctol) istop = 3;
+  if (test2 <= atol) istop = 2;
+  if (test1 <= rtol) istop = 1;
+  scal[S_ISTOP] = istop;
+  if (istop != 0) scal[S_DONE] = 1.0;
+}
+
+__global__ void k_sumsq(int64_t n, const double* __restrict__ a, double* scal, int slot,
+                        double* part, unsigned int* counter) {
+  double s2 = 0.0, z0 = 0.0, z1 = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    s2 = __fma_rn(a[j], a[j], s2);
+  if (grid_sum3(s2, z0, z1, part, counter) && threadIdx.x == 0) scal[slot] = s2;
+}
+
+__global__ void k_scale_setup(int64_t n, int mode, const double* __restrict__ colnorm,
+                              const double* __restrict__ user, double* __restrict__ d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double s = 1.0;
+    if (mode == GSR_PRECOND_COLNORM) {
+      const double c = colnorm[j];
+      s = c > 0.0 ? 1.0 / c : 1.0;
+    } else if (mode == GSR_PRECOND_USER) {
+      s = user[j];
+    }
+    d[j] = s;
+  }
+}
+
+// x = D z (de-precondition, Sec. 2 solver step 5); var = D^2 var.
+__global__ void k_finish(int64_t n, const double* __restrict__ d, const double* __restrict__ xz,
+                         double* __restrict__ x, double* __restrict__ var) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double dj = d[j];
+    x[j] = dj * xz[j];
+    if (var) var[j] *= dj * dj;
+  }
+}
+
+__global__ void k_zero(int64_t n, double* __restrict__ a, const double* scal) {
+  if (scal && scal[S_DONE] != 0.0) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    a[j] = 0.0;
+}
+
+namespace {
+
+int ensure_work(gsr_system* s) {
+  if (s->u) return GSR_OK;
+  const int64_t n = s->L.n_rows, m = s->L.n_unk;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 8);
+  };
+  A((void**)&s->u, n * 8);
+  A((void**)&s->u_knot, n * 8);
+  A((void**)&s->v, m * 8);
+  A((void**)&s->w, m * 8);
+  A((void**)&s->xz, m * 8);
+  A((void**)&s->z, m * 8);
+  A((void**)&s->dscale, m * 8);
+  A((void**)&s->v_ff, m * 8);
+  A((void**)&s->scal, S_COUNT * 8);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_scal, S_COUNT * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
+  }
+  return GSR_OK;
+}
+
+struct Ctx {
+  gsr_system* s;
+  cudaStream_t st;
+  int which_values;
+  double* var;
+  const double* x_ref;
+  double* err_dev;
+  double* rn_dev;
+};
+
+constexpr int LAUNCHES_PER_ITERATION = 6;  // aprod1, zero, aprod2 (2), vec_a, vec_b
+
+// Events (4 per iteration) bracket aprod 1, aprod 2 and the vector kernels.
+int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
+  gsr_system* s = c.s;
+  const Layout& L = s->L;
+  double* scal = s->scal;
+  const int vb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_unk + 255) / 256 + 1);
+  if (ev) cudaEventRecordWithFlags(ev[0], c.st, cudaEventRecordExternal);
+  int rc = launch_aprod1(s, c.which_values, s->v_ff, s->u, scal + S_COEF_U, 0.0, s->u_knot,
+                         scal + S_UNORM2, scal + S_DONE, c.st);
+  if (rc != GSR_OK) return rc;
+  k_zero<<<vb, 256, 0, c.st>>>(L.n_unk, s->z, scal);
+  if (ev) cudaEventRecordWithFlags(ev[1], c.st, cudaEventRecordExternal);
+  rc = launch_aprod2(s, c.which_values, s->u, s->u_knot, s->z, scal + S_DONE, c.st);
+  if (rc != GSR_OK) return rc;
+  if (ev) cudaEventRecordWithFlags(ev[2], c.st, cudaEventRecordExternal);
+  k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 0);
+  k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
+                                scal, s->S.red, s->S.count + 2, 0, c.err_dev, c.rn_dev);
+  if (ev) cudaEventRecordWithFlags(ev[3], c.st, cudaEventRecordExternal);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
+             gsr_lsqr_result* res, cudaStream_t st, int which_values, bool keep_state,
+             int64_t itnlim) {
+  (void)keep_state;
+  const Layout& L = s->L;
+  const int vb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_unk + 255) / 256 + 1);
+  const int rb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_rows + 255) / 256 + 1);
+  double* scal = s->scal;
+  cudaError_t e = cudaSuccess;
+  auto C = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  // scalars
+  double h[S_COUNT];
+  std::memset(h, 0, sizeof(h));
+  h[S_ATOL] = o->atol;
+  h[S_BTOL] = o->btol;
+  h[S_CTOL] = o->conlim > 0.0 ? 1.0 / o->conlim : 0.0;
+  h[S_ITNLIM] = (double)itnlim;
+  C(cudaMemcpyAsync(scal, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  C(cudaStreamSynchronize(st));  // h is a stack buffer
+  // per-iteration histories
+  double* err_dev = nullptr;
+  double* rn_dev = nullptr;
+  if (o->err_hist && o->x_ref) C(cudaMallocAsync((void**)&err_dev, itnlim * 8 + 8, st));
+  if (o->rnorm_hist) C(cudaMallocAsync((void**)&rn_dev, itnlim * 8 + 8, st));
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  if (o->x_ref && err_dev)
+    k_sumsq<<<vb, 256, 0, st>>>(L.n_unk, o->x_ref, scal, S_XREF2, s->S.red, s->S.count + 3);
+  if (o->var) k_zero<<<vb, 256, 0, st>>>(L.n_unk, o->var, nullptr);
+  k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->xz, nullptr);
+  // start: beta_1 u_1 = b, alpha_1 v_1 = (A D)^T u_1, w_1 = v_1, x_0 = 0
+  k_init_u<<<rb, 256, 0, st>>>(L, b, s->u, s->u_knot, scal, s->S.red, s->S.count + 4);
+  k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->z, nullptr);
+  int rc = launch_aprod2(s, which_values, s->u, s->u_knot, s->z, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  k_vec_a<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 1);
+  k_vec_b<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, o->var,
+                              o->x_ref && err_dev ? o->x_ref : nullptr, scal, s->S.red,
+                              s->S.count + 2, 1, nullptr, nullptr);
+  C(cudaGetLastError());
+  if (e != cudaSuccess) return GSR_E_CUDA;
+
+  int64_t n_launches = 7 + (o->var ? 1 : 0) + ((o->x_ref && err_dev) ? 1 : 0);
+  Ctx c{s, st, which_values, o->var, (o->x_ref && err_dev) ? o->x_ref : nullptr, err_dev, rn_dev};
+  // Capture a chunk of iterations once and replay it.
+  const int chunk = 4;
+  const bool prof = o->profile != 0;
+  cudaEvent_t evs[4 * chunk];
+  int n_ev = 0;
+  if (prof) {
+    for (; n_ev < 4 * chunk; ++n_ev)
+      if (cudaEventCreate(&evs[n_ev]) != cudaSuccess) break;
+    if (n_ev < 4 * chunk) {
+      for (int i = 0; i < n_ev; ++i) cudaEventDestroy(evs[i]);
+      return GSR_E_CUDA;
+    }
+  }
+  double t_a1 = 0.0, t_a2 = 0.0, t_vec = 0.0;
+  int64_t timed = 0, itn_seen = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      use_graph = false;
+  }
+  if (use_graph && st != nullptr) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int r2 = GSR_OK;
+      for (int i = 0; i < chunk && r2 == GSR_OK; ++i) r2 = enqueue_iteration(c, prof ? evs + 4 * i : nullptr);
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (r2 != GSR_OK || ce != cudaSuccess ||
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        graph = nullptr;
+        exec = nullptr;
+        use_graph = false;
+      }
+    } else {
+      cudaGetLastError();
+      use_graph = false;
+    }
+  } else {
+    use_graph = false;
+  }
+  int64_t launched = 0;
+  while (true) {
+    if (use_graph) {
+      C(cudaGraphLaunch(exec, st));
+    } else {
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i) {
+        rc = enqueue_iteration(c, prof ? evs + 4 * i : nullptr);
+        if (rc != GSR_OK) break;
+      }
+    }
+    launched += chunk;
+    n_launches += (int64_t)chunk * LAUNCHES_PER_ITERATION;
+    C(cudaMemcpyAsync(s->host_scal, scal, S_COUNT * 8, cudaMemcpyDeviceToHost, st));
+    C(cudaStreamSynchronize(st));
+    if (e != cudaSuccess || rc != GSR_OK) break;
+    if (prof) {
+      // iterations of this chunk that did work (the rest returned at once)
+      const int64_t itn_now = (int64_t)s->host_scal[S_ITN];
+      const int64_t worked = std::min<int64_t>(chunk, itn_now - itn_seen);
+      for (int i = 0; i < worked; ++i) {
+        float a = 0.f, b2 = 0.f, v = 0.f;
+        C(cudaEventElapsedTime(&a, evs[4 * i], evs[4 * i + 1]));
+        C(cudaEventElapsedTime(&b2, evs[4 * i + 1], evs[4 * i + 2]));
+        C(cudaEventElapsedTime(&v, evs[4 * i + 2], evs[4 * i + 3]));
+        t_a1 += a;
+        t_a2 += b2;
+        t_vec += v;
+      }
+      timed += worked > 0 ? worked : 0;
+      itn_seen = itn_now;
+    }
+    if (s->host_scal[S_DONE] != 0.0) break;
+    if (launched > itnlim + chunk) break;  // cannot happen: istop = 7 at itnlim
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int i = 0; i < n_ev; ++i) cudaEventDestroy(evs[i]);
+  if (e != cudaSuccess || rc != GSR_OK) {
+    if (err_dev) cudaFreeAsync(err_dev, st);
+    if (rn_dev) cudaFreeAsync(rn_dev, st);
+    return rc != GSR_OK ? rc : GSR_E_CUDA;
+  }
+  const double* hs = s->host_scal;
+  const int64_t itn = (int64_t)hs[S_ITN];
+  if (x) k_finish<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->xz, x, o->var);
+  if (o->err_hist && err_dev && itn > 0)
+    C(cudaMemcpyAsync(o->err_hist, err_dev, itn * 8, cudaMemcpyDeviceToHost, st));
+  if (o->rnorm_hist && rn_dev && itn > 0)
+    C(cudaMemcpyAsync(o->rnorm_hist, rn_dev, itn * 8, cudaMemcpyDeviceToHost, st));
+  if (err_dev) C(cudaFreeAsync(err_dev, st));
+  if (rn_dev) C(cudaFreeAsync(rn_dev, st));
+  C(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  res->istop = (int32_t)hs[S_ISTOP];
+  res->itn = itn;
+  res->rnorm = hs[S_RNORM];
+  res->arnorm = hs[S_ARNORM];
+  res->anorm = std::sqrt(hs[S_ANORM2]);
+  res->acond = hs[S_ACOND];
+  res->xnorm = hs[S_XNORM];
+  res->n_launches = n_launches + (x ? 1 : 0);
+  res->n_timed_itn = timed;
+  res->t_aprod1_ms = t_a1;
+  res->t_aprod2_ms = t_a2;
+  res->t_vector_ms = t_vec;
+  return GSR_OK;
+}
+
+int setup_scaling(gsr_system* s, const gsr_lsqr_opts* o, cudaStream_t st) {
+  const int vb = (int)std::min<int64_t>(RED_BLOCKS, (s->L.n_unk + 255) / 256 + 1);
+  k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->dscale);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace gsr
+
+extern "C" {
+
+void gsr_lsqr_default_opts(gsr_lsqr_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->atol = 1e-12;
+  o->btol = 1e-12;
+  o->conlim = 1e12;
+  o->itnlim = 0;
+  o->precond = GSR_PRECOND_COLNORM;
+  o->precision = GSR_PREC_F64;
+}
+
+int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_opts* opts,
+                   gsr_lsqr_result* res, void* stream) {
+  if (!sys || !opts || !res) return GSR_E_ARG;
+  if ((!b && sys->L.n_rows > 0) || (!x && sys->L.n_unk > 0)) return GSR_E_ARG;
+  if (opts->precond < GSR_PRECOND_NONE || opts->precond > GSR_PRECOND_USER) return GSR_E_ARG;
+  if (opts->precond == GSR_PRECOND_USER && !opts->scale) return GSR_E_ARG;
+  if (opts->precision != GSR_PREC_F64 && opts->precision != GSR_PREC_MIXED) return GSR_E_ARG;
+  if (opts->precision == GSR_PREC_MIXED && !sys->vals_f32) return GSR_E_ARG;
+  if (opts->atol < 0 || opts->btol < 0 || opts->conlim < 0 || opts->itnlim < 0) return GSR_E_ARG;
+  if ((opts->err_hist && !opts->x_ref)) return GSR_E_ARG;
+  std::memset(res, 0, sizeof(*res));
+  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = gsr::ensure_work(sys);
+  if (rc != GSR_OK) return rc;
+  rc = gsr::setup_scaling(sys, opts, st);
+  if (rc != GSR_OK) return rc;
+  const int64_t itnlim = opts->itnlim > 0 ? opts->itnlim : 20 * std::max<int64_t>(1, sys->L.n_unk);
+  if (sys->L.n_rows == 0 || sys->L.n_unk == 0) {
+    if (x && sys->L.n_unk > 0) cudaMemsetAsync(x, 0, sys->L.n_unk * 8, st);
+    res->istop = 0;
+    return gsr::cuda_status(cudaStreamSynchronize(st));
+  }
+  return gsr::lsqr_run(sys, b, x, opts, res, st, GSR_VALUES_F64, false, itnlim);
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+"""Python binding over the C ABI of libgsr (include/gsr.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libgsr.so. Device vectors are torch tensors (float64, contiguous,
+on the system's device); the current torch stream is passed to every call.
+There is no CPU fallback: if libgsr.so is missing or fails to load, importing
+this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_c_i64 = ctypes.c_int64
+_c_i32 = ctypes.c_int32
+_c_dbl = ctypes.c_double
+_c_p = ctypes.c_void_p
+
+STATUS = {0: "GSR_OK", 1: "GSR_E_ARG", 2: "GSR_E_INDEX", 3: "GSR_E_UNSORTED",
+          4: "GSR_E_NONFINITE", 5: "GSR_E_OOM", 6: "GSR_E_CUDA", 7: "GSR_E_TIMEOUT",
+          8: "GSR_E_UNSUPPORTED"}
+VALUES_F64, VALUES_F32 = 0, 1
+STORE_F64, STORE_F32_PLUS_F64 = 0, 1
+PRECOND = {"none": 0, "colnorm": 1, "user": 2}
+PRECISION = {"f64": 0, "mixed": 1}
+
+
+class GsrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%s)" % (where, STATUS.get(code, code), strerror(code)))
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("n_rows", _c_i64), ("n_stars", _c_i64), ("n_knots", _c_i64),
+                ("n_instr", _c_i64), ("n_glob", _c_i32), ("storage", _c_i32)]
+
+
+class LsqrOpts(ctypes.Structure):
+    _fields_ = [("atol", _c_dbl), ("btol", _c_dbl), ("conlim", _c_dbl), ("itnlim", _c_i64),
+                ("precond", _c_i32), ("precision", _c_i32), ("scale", _c_p), ("var", _c_p),
+                ("x_ref", _c_p), ("err_hist", _c_p), ("rnorm_hist", _c_p),
+                ("mixed_switch_itn", _c_i32), ("profile", _c_i32)]
+
+
+class LsqrResult(ctypes.Structure):
+    _fields_ = [("istop", _c_i32), ("phase2_itn", _c_i32), ("itn", _c_i64), ("rnorm", _c_dbl),
+                ("arnorm", _c_dbl), ("anorm", _c_dbl), ("acond", _c_dbl), ("xnorm", _c_dbl),
+                ("n_launches", _c_i64), ("n_timed_itn", _c_i64), ("t_aprod1_ms", _c_dbl),
+                ("t_aprod2_ms", _c_dbl), ("t_vector_ms", _c_dbl)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libgsr.so not built (%s); run paper_2503_22863_b300/build.py or "
+                          "__graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    lib.gsr_create.argtypes = [ctypes.POINTER(Dims), _c_p, _c_p, _c_p, _c_p, ctypes.c_int, _c_p,
+                               ctypes.POINTER(_c_p)]
+    lib.gsr_create.restype = ctypes.c_int
+    lib.gsr_destroy.argtypes = [_c_p]
+    lib.gsr_destroy.restype = None
+    lib.gsr_strerror.argtypes = [ctypes.c_int]
+    lib.gsr_strerror.restype = ctypes.c_char_p
+    lib.gsr_n_unknowns.argtypes = [_c_p]
+    lib.gsr_n_unknowns.restype = _c_i64
+    lib.gsr_n_rows.argtypes = [_c_p]
+    lib.gsr_n_rows.restype = _c_i64
+    for name in ("gsr_aprod1", "gsr_aprod2"):
+        getattr(lib, name).argtypes = [_c_p, _c_p, _c_p, _c_p]
+        getattr(lib, name).restype = ctypes.c_int
+    for name in ("gsr_aprod1_values", "gsr_aprod2_values"):
+        getattr(lib, name).argtypes = [_c_p, ctypes.c_int, _c_p, _c_p, _c_p]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.gsr_column_norms.argtypes = [_c_p, _c_p, _c_p]
+    lib.gsr_column_norms.restype = ctypes.c_int
+    lib.gsr_lsqr_default_opts.argtypes = [ctypes.POINTER(LsqrOpts)]
+    lib.gsr_lsqr_default_opts.restype = None
+    lib.gsr_lsqr_solve.argtypes = [_c_p, _c_p, _c_p, ctypes.POINTER(LsqrOpts),
+                                   ctypes.POINTER(LsqrResult), _c_p]
+    lib.gsr_lsqr_solve.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def strerror(code):
+    return lib.gsr_strerror(int(code)).decode()
+
+
+def _check(code, where):
+    if code != 0:
+        raise GsrError(code, where)
+
+
+def _stream():
+    return _c_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, n, name, dtype=torch.float64):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be a contiguous %s tensor with %d elements" % (name, dtype, n))
+    return _c_p(t.data_ptr())
+
+
+class System:
+    """A packed AVU-GSR system resident on one GPU (wraps gsr_create/gsr_destroy)."""
+
+    def __init__(self, sys, device=0, storage="f64"):
+        vals = np.ascontiguousarray(sys["vals"], dtype=np.float64)
+        ao = np.ascontiguousarray(sys["astro_off"], dtype=np.int64)
+        at = np.ascontiguousarray(sys["att_off"], dtype=np.int64)
+        ins = np.ascontiguousarray(sys["instr"], dtype=np.int32)
+        self.device = torch.device("cuda", device)
+        d = Dims(int(sys["n_rows"]), int(sys["n_stars"]), int(sys["n_knots"]),
+                 int(sys["n_instr"]), int(sys["n_glob"]),
+                 STORE_F32_PLUS_F64 if storage == "f32+f64" else STORE_F64)
+        h = _c_p()
+        with torch.cuda.device(self.device):
+            code = lib.gsr_create(ctypes.byref(d), vals.ctypes.data_as(_c_p),
+                                  ao.ctypes.data_as(_c_p), at.ctypes.data_as(_c_p),
+                                  ins.ctypes.data_as(_c_p), int(device), _stream(),
+                                  ctypes.byref(h))
+        _check(code, "gsr_create")
+        self._h = h
+        self.n_rows = int(lib.gsr_n_rows(h))
+        self.n_unk = int(lib.gsr_n_unknowns(h))
+        self.storage = storage
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.gsr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def aprod1(self, x, y, values="f64"):
+        """Eq. 2: y += A x (in place on the tensor y)."""
+        code = lib.gsr_aprod1_values(self._h, VALUES_F32 if values == "f32" else VALUES_F64,
+                                     _dptr(x, self.n_unk, "x"), _dptr(y, self.n_rows, "y"),
+                                     _stream())
+        _check(code, "gsr_aprod1")
+        return y
+
+    def aprod2(self, y, x, values="f64"):
+        """Eq. 3: x += A^T y (in place on the tensor x)."""
+        code = lib.gsr_aprod2_values(self._h, VALUES_F32 if values == "f32" else VALUES_F64,
+                                     _dptr(y, self.n_rows, "y"), _dptr(x, self.n_unk, "x"),
+                                     _stream())
+        _check(code, "gsr_aprod2")
+        return x
+
+    def column_norms(self):
+        c = torch.empty(self.n_unk, dtype=torch.float64, device=self.device)
+        _check(lib.gsr_column_norms(self._h, _c_p(c.data_ptr()), _stream()), "gsr_column_norms")
+        return c
+
+    def lsqr(self, b, x=None, atol=1e-12, btol=1e-12, conlim=1e12, itnlim=0, precond="colnorm",
+             precision="f64", scale=None, want_var=False, x_ref=None, err_hist=False,
+             rnorm_hist=False, mixed_switch_itn=0, profile=False):
+        """Preconditioned LSQR (gsr_lsqr_solve). Returns a dict with x and the result fields."""
+        o = LsqrOpts()
+        lib.gsr_lsqr_default_opts(ctypes.byref(o))
+        o.atol, o.btol, o.conlim, o.itnlim = atol, btol, conlim, int(itnlim)
+        o.precond = PRECOND[precond]
+        o.precision = PRECISION[precision]
+        o.mixed_switch_itn = int(mixed_switch_itn)
+        o.profile = 1 if profile else 0
+        if scale is not None:
+            o.scale = _dptr(scale, self.n_unk, "scale").value
+        var = None
+        if want_var:
+            var = torch.zeros(self.n_unk, dtype=torch.float64, device=self.device)
+            o.var = var.data_ptr()
+        if x_ref is not None:
+            o.x_ref = _dptr(x_ref, self.n_unk, "x_ref").value
+        lim = int(itnlim) if itnlim else 20 * max(1, self.n_unk)
+        eh = rh = None
+        if err_hist:
+            if x_ref is None:
+                raise ValueError("err_hist needs x_ref")
+            eh = np.full(lim, np.nan)
+            o.err_hist = eh.ctypes.data
+        if rnorm_hist:
+            rh = np.full(lim, np.nan)
+            o.rnorm_hist = rh.ctypes.data
+        if x is None:
+            x = torch.empty(self.n_unk, dtype=torch.float64, device=self.device)
+        r = LsqrResult()
+        code = lib.gsr_lsqr_solve(self._h, _dptr(b, self.n_rows, "b"), _dptr(x, self.n_unk, "x"),
+                                  ctypes.byref(o), ctypes.byref(r), _stream())
+        _check(code, "gsr_lsqr_solve")
+        out = dict(x=x, istop=r.istop, itn=r.itn, phase2_itn=r.phase2_itn, rnorm=r.rnorm,
+                   arnorm=r.arnorm, anorm=r.anorm, acond=r.acond, xnorm=r.xnorm,
+                   n_launches=r.n_launches, n_timed_itn=r.n_timed_itn,
+                   t_aprod1_ms=r.t_aprod1_ms, t_aprod2_ms=r.t_aprod2_ms,
+                   t_vector_ms=r.t_vector_ms)
+        if var is not None:
+            out["var"] = var
+        if eh is not None:
+            out["err_hist"] = eh[:r.itn]
+        if rh is not None:
+            out["rnorm_hist"] = rh[:r.itn]
+        return out

@@ -35,6 +35,10 @@ CONFIGS = {
                    n_glob=1, seed=2504),
     "large": dict(n_stars=4_000_000, obs=40, poisson=True, n_knots=200_000, n_instr=20_000,
                   n_glob=1, seed=2505),
+    # profiling case: the medium shape at 1/10 of the rows (~1 GB on the device,
+    # still well above the 126 MB L2)
+    "small": dict(n_stars=100_000, obs=30, poisson=True, n_knots=20_000, n_instr=2_000,
+                  n_glob=1, seed=2510),
 }
 NOISE_SIGMA = 1e-3
 

@@ -1,0 +1,99 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and
+its host-side validation returns the documented codes (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsr_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def gsr():
+    from paper_2503_22863_b300 import build
+    build.build()
+    from paper_2503_22863_b300 import gsr as g
+    return g
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("gsr_create", "gsr_aprod1", "gsr_aprod2", "gsr_lsqr_solve", "gsr_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(gsr):
+    lib = ctypes.CDLL(gsr._build.LIB)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_defaults(gsr):
+    assert gsr.strerror(0) == "ok"
+    assert "sorted" in gsr.strerror(3)
+    o = gsr.LsqrOpts()
+    gsr.lib.gsr_lsqr_default_opts(ctypes.byref(o))
+    assert o.atol == 1e-12 and o.btol == 1e-12 and o.precond == 1 and o.precision == 0
+
+
+def _tiny(n_glob=1):
+    from paper_2503_22863_b300 import synth
+    return synth.make_system(n_stars=10, n_knots=8, n_instr=7, n_glob=n_glob, obs=6,
+                             poisson=False, seed=3)
+
+
+def _create(gsr, sys, **over):
+    d = gsr.Dims(sys["n_rows"], sys["n_stars"], sys["n_knots"], sys["n_instr"], sys["n_glob"], 0)
+    for k, v in over.items():
+        setattr(d, k, v)
+    vals = np.ascontiguousarray(sys["vals"])
+    ao = np.ascontiguousarray(sys["astro_off"])
+    at = np.ascontiguousarray(sys["att_off"])
+    ins = np.ascontiguousarray(sys["instr"])
+    h = ctypes.c_void_p()
+    code = gsr.lib.gsr_create(ctypes.byref(d), vals.ctypes.data_as(ctypes.c_void_p),
+                              ao.ctypes.data_as(ctypes.c_void_p), at.ctypes.data_as(ctypes.c_void_p),
+                              ins.ctypes.data_as(ctypes.c_void_p), 0, None, ctypes.byref(h))
+    if code == 0:
+        gsr.lib.gsr_destroy(h)
+    return code
+
+
+def test_create_rejects_bad_inputs_on_host(gsr):
+    base = _tiny()
+    assert _create(gsr, base, n_knots=3) == 1          # GSR_E_ARG
+    assert _create(gsr, base, n_instr=5) == 1
+    assert _create(gsr, base, n_glob=2) == 1
+    assert _create(gsr, base, n_instr=70000) == 8       # GSR_E_UNSUPPORTED
+    s = dict(base, astro_off=base["astro_off"].copy())
+    s["astro_off"][3] = 7                               # not a multiple of 5
+    assert _create(gsr, s) == 2
+    s = dict(base, astro_off=base["astro_off"][::-1].copy())
+    assert _create(gsr, s) == 3                         # GSR_E_UNSORTED
+    s = dict(base, att_off=base["att_off"].copy())
+    s["att_off"][0] = 5 * 10 + 5                        # s = 5 > K - 4 = 4
+    assert _create(gsr, s) == 2
+    s = dict(base, instr=base["instr"].copy())
+    s["instr"][1, 2] = s["instr"][1, 1]                 # repeated instrumental column
+    assert _create(gsr, s) == 2
+    s = dict(base, instr=base["instr"].copy())
+    s["instr"][0, 5] = 7                                # outside [0, n_instr)
+    assert _create(gsr, s) == 2
+    s = dict(base, vals=base["vals"].copy())
+    s["vals"][4, 9] = np.nan
+    assert _create(gsr, s) == 4                         # GSR_E_NONFINITE
+    # an ignored global slot may hold anything when n_glob = 0
+    s0 = _tiny(n_glob=0)
+    s0 = dict(s0, vals=s0["vals"].copy())
+    s0["vals"][:, 23] = np.inf
+    s0["vals"][0, 0] = np.nan
+    assert _create(gsr, s0) == 4

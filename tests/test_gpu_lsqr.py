@@ -1,0 +1,128 @@
+"""GPU parity of the preconditioned LSQR against the FP64 CPU oracle.
+
+The bar: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-9, with x_oracle from the
+oracle run to atol = btol = 1e-14. Mid-run iterates are not compared (their
+sensitivity to rounding order is intrinsic to the recurrence); solutions,
+stopping codes, estimates and invariants are."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_22863_b300 import synth
+from gpu_util import LSQR_TOL, rhs, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gsr():
+    from paper_2503_22863_b300 import gsr as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    sys = synth.make_config("tiny")
+    b = rhs(sys)
+    ref = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
+    return sys, b, ref
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_lsqr_tiny_matches_oracle(gsr, tiny):
+    sys, b, ref = tiny
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14)
+        x = to_host(r["x"])
+    assert r["istop"] in (1, 2, 4, 5), r["istop"]
+    assert relerr(x, ref["x"]) <= LSQR_TOL
+    assert abs(r["itn"] - ref["itn"]) <= 3
+    assert abs(r["rnorm"] - ref["rnorm"]) <= 1e-9 * ref["rnorm"]
+    assert abs(r["anorm"] - ref["anorm"]) <= 1e-9 * ref["anorm"]
+
+
+def test_lsqr_tiny_default_tolerance(gsr, tiny):
+    sys, b, ref = tiny
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-12, btol=1e-12)
+    o = oracle.lsqr(sys, b, atol=1e-12, btol=1e-12)
+    assert r["istop"] == o["istop"]
+    assert abs(r["itn"] - o["itn"]) <= 2
+    assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
+
+
+@pytest.mark.parametrize("precond", ["none", "colnorm", "user"])
+def test_lsqr_preconditioners_same_answer(gsr, precond):
+    sys = synth.make_system(n_stars=300, n_knots=80, n_instr=30, n_glob=1, obs=25, seed=21)
+    b = rhs(sys)
+    ref = oracle.lsqr(sys, b, atol=1e-15, btol=1e-15)
+    scale = None
+    if precond == "user":
+        scale = to_dev(np.exp(np.random.default_rng(2).uniform(-0.5, 0.5, sys["n_unk"])))
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-15, btol=1e-15, precond=precond, scale=scale,
+                   itnlim=5000)
+    assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
+
+
+def test_lsqr_planted_solution(gsr):
+    sys = synth.make_system(n_stars=2000, n_knots=300, n_instr=100, n_glob=0, obs=20, seed=22,
+                            x_star="ones")
+    b = np.zeros(sys["n_rows"])
+    oracle.aprod1(sys, sys["x_star"], b)
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14)
+    assert np.max(np.abs(to_host(r["x"]) - 1.0)) < 1e-9
+
+
+def test_lsqr_zero_rhs_and_itnlim(gsr):
+    sys = synth.make_system(n_stars=100, n_knots=20, n_instr=10, n_glob=1, obs=12, seed=23)
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(np.zeros(sys["n_rows"])))
+        assert r["istop"] == 0 and r["itn"] == 0
+        assert not to_host(r["x"]).any()
+        b = rhs(sys)
+        r = S.lsqr(to_dev(b), atol=0.0, btol=0.0, conlim=0.0, itnlim=7)
+        assert r["istop"] == 7 and r["itn"] == 7
+        o = oracle.lsqr(sys, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=7)
+        # 7 well-conditioned (column-scaled) steps: iterates still agree closely
+        assert relerr(to_host(r["x"]), o["x"]) < 1e-10
+
+
+def test_lsqr_error_history_and_variance(gsr, tiny):
+    sys, b, ref = tiny
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, x_ref=to_dev(ref["x"]), err_hist=True,
+                   rnorm_hist=True, want_var=True)
+    eh = r["err_hist"]
+    assert eh.size == r["itn"] and eh[-1] <= LSQR_TOL
+    assert (np.diff(r["rnorm_hist"]) <= 1e-12 * r["rnorm_hist"][0]).all()
+    o = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14, want_var=True)
+    var = to_host(r["var"])
+    # the variance estimate is a sum over the run; both runs take nearly the same steps
+    assert np.max(np.abs(var - o["var"]) / o["var"]) < 1e-3
+
+
+def test_lsqr_medium_normal_equations(gsr):
+    """The 30M-row workload: the GPU solution satisfies the normal equations, checked
+    with the oracle's own aprods at full size."""
+    sys = synth.make_config("medium")
+    b = rhs(sys)
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-12, btol=1e-12)
+        x = to_host(r["x"])
+    assert r["istop"] in (1, 2)
+    res = b.copy()
+    oracle.aprod1(sys, -x, res)           # r = b - A x
+    atr = np.zeros(sys["n_unk"])
+    oracle.aprod2(sys, res, atr)
+    # column-scaled test: ||D A^T r|| / (||A D||_F ||r||) as LSQR's test 2 measures it
+    c = np.sqrt(oracle.colnorm2(sys))
+    d = np.where(c > 0, 1.0 / np.where(c > 0, c, 1.0), 1.0)
+    anorm_scaled = np.sqrt(np.count_nonzero(c))
+    test2 = np.linalg.norm(d * atr) / (anorm_scaled * np.linalg.norm(res))
+    assert test2 <= 1e-10, test2
