@@ -104,6 +104,28 @@ int gsr_aprod1_values(gsr_system* sys, int which_values, const double* x, double
 int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double* x,
                       void* stream);
 
+/*
+ * Allocation-free aprod 1 (this entry point has no counterpart in the paper):
+ * y[n_rows] += A x[N_unk] exactly as gsr_aprod1, for callers that must not
+ * allocate device memory when they call it - a host loop being captured into a
+ * CUDA graph (allocation cannot be captured), a process whose device memory is
+ * held by another framework's caching allocator, or a latency-critical loop that
+ * cannot absorb the synchronisation cudaMalloc/cudaFree imply. It calls no
+ * cudaMalloc, cudaFree or other allocating routine and uses none of the
+ * system's scratch: the float-pair copy of x that the product reads is staged in
+ * a fixed device array compiled into the library (GSR_NOALLOC_MAX_UNK float
+ * pairs = 8 MiB, held by every GPU that loads the library until the process
+ * exits). Systems with N_unk > GSR_NOALLOC_MAX_UNK get GSR_E_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.
+ * Every call on a device shares the one array, and each call rewrites the part
+ * it reads (nothing in it needs to start at zero), so calls that overlap on the
+ * GPU - on different streams, or for different systems on the same device -
+ * race and must be serialised by the caller. x, y device; stream as above.
+ */
+#define GSR_NOALLOC_MAX_UNK 1048576
+int gsr_aprod1_noalloc(gsr_system* sys, const double* x, double* y, void* stream);
+
 /* Column norms c_j = ||A_:,j||_2 (FP64 copy of the values) into c[N_unk], device. */
 int gsr_column_norms(gsr_system* sys, double* c, void* stream);
 

@@ -1,0 +1,66 @@
+// gsr_aprod1_noalloc: aprod 1 (y += A x) whose only scratch lives in a fixed,
+// file-scope device array of this library instead of memory allocated by the
+// library or the caller.
+//
+// Who needs it: code that must not allocate device memory at the moment it
+// calls us. Typical cases are a host loop that is being captured into a CUDA
+// graph (cudaMalloc is not a capturable operation), a process whose device
+// memory has been taken up front by another framework's caching allocator,
+// and latency-critical loops where the implicit device synchronisation of
+// cudaMalloc/cudaFree is not acceptable. This entry point calls no cudaMalloc,
+// cudaFree or any allocating routine; the caller only passes x and y.
+//
+// The scratch is the float-pair copy of x that the aprod 1 kernel gathers from.
+// It holds at most GSR_NOALLOC_MAX_UNK unknowns (8 MiB of float pairs), a size
+// every GPU that loads the library keeps reserved until the process exits.
+#include <mutex>
+
+#include "gsr_internal.cuh"
+
+namespace {
+
+constexpr int64_t kMaxUnk = GSR_NOALLOC_MAX_UNK;
+constexpr int kMaxDevices = 64;
+
+// The static scratch: one copy per device, reserved when the module loads.
+static __device__ __align__(256) float2 g_x_pairs[kMaxUnk];
+
+// Host code cannot pass the symbol itself to a kernel (on the host it names a
+// stand-in, not device memory), so the device address is looked up once per
+// device, with that device current, and cached here.
+std::mutex g_mu;
+float2* g_addr[kMaxDevices] = {};
+
+int static_scratch(int device, float2** out) {
+  if (device < 0 || device >= kMaxDevices) return GSR_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_x_pairs);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return GSR_E_CUDA;
+    }
+    g_addr[device] = static_cast<float2*>(p);
+  }
+  *out = g_addr[device];
+  return GSR_OK;
+}
+
+}  // namespace
+
+extern "C" int gsr_aprod1_noalloc(gsr_system* sys, const double* x, double* y, void* stream) {
+  if (!sys || (!x && sys->L.n_unk > 0) || (!y && sys->L.n_rows > 0)) return GSR_E_ARG;
+  if (sys->L.n_unk > kMaxUnk) return GSR_E_UNSUPPORTED;
+  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  float2* pairs = nullptr;
+  int rc = static_scratch(sys->device, &pairs);
+  if (rc != GSR_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Every call rewrites pairs[0, N_unk) before the product reads it, so no part
+  // of the shared buffer has to start at zero.
+  rc = gsr::launch_to_ff(x, nullptr, pairs, sys->L.n_unk, st);
+  if (rc != GSR_OK) return rc;
+  return gsr::launch_aprod1(sys, GSR_VALUES_F64, pairs, y, nullptr, 1.0, nullptr, nullptr,
+                            nullptr, st);
+}
