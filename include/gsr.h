@@ -80,7 +80,7 @@ typedef struct {
  * 0/1), GSR_E_INDEX (astro_off not 5*star in range, s_i outside [0, K-4],
  * instr outside [0, n_instr) or repeated in a row), GSR_E_UNSORTED (astro_off
  * decreasing), GSR_E_NONFINITE (NaN/Inf value), GSR_E_UNSUPPORTED (n_rows or
- * N_unk >= 2^31, or n_instr > 28672: the instrumental histogram of aprod 2
+ * N_unk >= 2^31, or n_instr > 24576: the instrumental histogram of aprod 2
  * lives in one block's shared memory), GSR_E_OOM.
  * On success *out owns everything; release it with gsr_destroy().
  */

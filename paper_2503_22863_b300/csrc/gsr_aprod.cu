@@ -1,10 +1,24 @@
 // aprod 1 (Eq. 2, y += A x) and aprod 2 (Eq. 3, x += A^T y) kernels for sm_103a.
 //
 // Both products are HBM-bound (about 0.2 flop per byte) and use no tensor
-// cores. B300's FP64 pipe runs at ~1/64 of its FP32 rate, so every product
-// and sum is done on the FP32 pipe as a float pair (hi, lo) with error-free
-// transformations; only a few FP64 operations per row remain (converting u,
-// forming the output, the norm).
+// cores. B300's FP64 pipe runs at ~1/64 of its FP32 rate, and double<->float
+// conversions issue on it too, so the hot loops contain no double-precision
+// instruction at all: products and sums are float pairs (hi, lo) with
+// error-free transformations, LSQR's u vector is kept as float pairs, and
+// results reach FP64 memory through exact bit-level float->double widening
+// and L2 atomics.
+//
+// aprod 1 streams 64-row records into shared memory with TMA bulk copies
+// (double-buffered per warp) so that DRAM latency is off the critical path;
+// the x gathers (L2-resident) are issued for both rows of a lane at once and
+// accumulated in six independent chains per row.
+// aprod 2 is three kernels that run concurrently on two streams:
+//   astro+glob  per-star sums over star-sorted records (segmented warp scan),
+//   instr       per tile of up to 2048 rows, entries in rounds of distinct
+//               bins added into a float-pair shared-memory histogram,
+//   att         start-knot-ordered copy, sliding 4-knot window per axis.
+#include <algorithm>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -50,8 +64,23 @@ __device__ void grid_sum_store(double v, double* part, unsigned int* counter, do
   }
 }
 
+// Exact widening of a float to double with integer operations only (no FP64
+// pipe). Subnormal floats (|f| < 2^-126) become zero.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)s, 0);
+  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
+  return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+// x += hi + lo as two L2 reductions (no FP64 arithmetic on the SM).
+__device__ __forceinline__ void red_ff(double* x, ff a) {
+  if (a.h != 0.0f) atomicAdd(x, f2d_bits(a.h));
+  if (a.l != 0.0f) atomicAdd(x, f2d_bits(a.l));
+}
+
 // ---------------------------------------------------------------------------
-// Element conversions.
+// Element conversions (only at the edges of the C ABI and of a solve).
 // ---------------------------------------------------------------------------
 __global__ void k_to_ff(const double* __restrict__ x, const double* __restrict__ scale,
                         float2* __restrict__ out, int64_t n) {
@@ -64,197 +93,280 @@ __global__ void k_to_ff(const double* __restrict__ x, const double* __restrict__
   }
 }
 
-__global__ void k_scatter_knot(Layout L, const double* __restrict__ y, double* __restrict__ y_knot) {
-  const int32_t* pos = reinterpret_cast<const int32_t*>(L.att_pos);
+// y (double) -> pairs in row order and in knot order.
+__global__ void k_to_ff_knot(Layout L, const double* __restrict__ y, float2* __restrict__ y_ff,
+                             float2* __restrict__ y_knot) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
-       r += (int64_t)gridDim.x * blockDim.x)
-    y_knot[pos[r]] = y[r];
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const ff f = ff_from_double(y[r]);
+    const float2 v = make_float2(f.h, f.l);
+    y_ff[r] = v;
+    y_knot[L.pos[r]] = v;
+  }
 }
 
-// Value of slot `t` for rows 4*lane + 2q + c of a tile, as a pair.
-template <bool F32>
-struct Vals;
+// X3[s*12 + a*4 + j] = x[att_base + a*K + s + j]: the 12 attitude unknowns a
+// row with start knot s multiplies, contiguous and 32-byte aligned per axis.
+__global__ void k_att_x3(Layout L, const float2* __restrict__ x, float2* __restrict__ x3,
+                         const double* stop) {
+  if (stop && *stop != 0.0) return;
+  const int64_t n = (L.n_knots - 3) * 12;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / 12;
+    const int a = (int)((i % 12) >> 2), j = (int)(i & 3);
+    x3[i] = __ldg(x + L.att_base + a * L.n_knots + s + j);
+  }
+}
 
-template <>
-struct Vals<false> {
-  float4 v;
-  __device__ __forceinline__ void load(const Layout& L, int64_t tile, int t, int q, int lane) {
-    v = __ldcs(L.vals_ff + ((tile * NSLOT + t) * 2 + q) * 32 + lane);
-  }
-  __device__ __forceinline__ ff get(int c) const {
-    return c == 0 ? ff{v.x, v.y} : ff{v.z, v.w};
-  }
-  __device__ __forceinline__ ff mul(int c, ff u) const { return ff_mul(get(c), u); }
-};
-
-template <>
-struct Vals<true> {
-  float2 v;
-  __device__ __forceinline__ void load(const Layout& L, int64_t tile, int t, int q, int lane) {
-    v = __ldcs(L.vals_f32 + ((tile * NSLOT + t) * 2 + q) * 32 + lane);
-  }
-  __device__ __forceinline__ ff mul(int c, ff u) const { return f_mul(c == 0 ? v.x : v.y, u); }
-};
+__device__ __forceinline__ ff ff_lo(double d) { return ff{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))}; }
 
 __device__ __forceinline__ ff ldx(const float2* __restrict__ x, int64_t j) {
-  float2 a = __ldg(x + j);
+  const float2 a = __ldg(x + j);
   return ff{a.x, a.y};
 }
 
-__device__ __forceinline__ int sel4(int4 a, int j) {
-  return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
+// Coefficient of slot t for row c (0/1) of the lane, from a record in smem or gmem.
+template <bool F32>
+__device__ __forceinline__ ff rec_val(const unsigned char* rec, int t, int lane, int c);
+template <>
+__device__ __forceinline__ ff rec_val<false>(const unsigned char* rec, int t, int lane, int c) {
+  const float4 v = *reinterpret_cast<const float4*>(rec + slot_offset<false>(t) + lane * 16);
+  return c == 0 ? ff{v.x, v.y} : ff{v.z, v.w};
 }
-__device__ __forceinline__ int sel4u(ushort4 a, int j) {
-  return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
+template <>
+__device__ __forceinline__ ff rec_val<true>(const unsigned char* rec, int t, int lane, int c) {
+  const float2 v = *reinterpret_cast<const float2*>(rec + slot_offset<true>(t) + lane * 8);
+  return ff{c == 0 ? v.x : v.y, 0.0f};
+}
+template <bool F32>
+__device__ __forceinline__ ff val_mul(ff v, ff u) {
+  if constexpr (F32) return f_mul(v.h, u);
+  else return ff_mul(v, u);
 }
 
 // ---------------------------------------------------------------------------
 // aprod 1: y[r] = coef * y[r] + (A x)[r] for every row; optionally
 // y_knot[pos(r)] = y[r] (the knot-ordered copy aprod 2 reads) and a
-// deterministic ||y||^2 into *norm_out. coef is *coef_dev if given.
-// One warp per 128-row tile (grid-stride over tiles), 4 rows per lane.
+// deterministic ||y||^2 into *norm_out. coef is *coef_dev if given. y is a
+// float-pair vector (YFF, LSQR) or a double vector (the C ABI).
+// One CTA per SM, NW warps; each warp owns NS record buffers in shared memory
+// that lane 0 refills with TMA while the warp computes on the previous one.
 // ---------------------------------------------------------------------------
-template <bool F32>
-__global__ void __launch_bounds__(256) k_aprod1(Layout L, const float2* __restrict__ x,
-                                                double* __restrict__ y,
-                                                const double* __restrict__ coef_dev,
-                                                double coef_host, double* __restrict__ y_knot,
-                                                double* part, unsigned int* counter,
-                                                double* norm_out, const double* stop) {
+template <bool F32, bool YFF, bool X3, int NW, int NS>
+__global__ void __launch_bounds__(NW * 32, 1)
+    k_aprod1(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
+             void* __restrict__ yv, const double* __restrict__ coef_dev, double coef_host,
+             float2* __restrict__ y_knot, double* part, unsigned int* counter, double* norm_out,
+             const double* stop, int instr_in_smem) {
   if (stop && *stop != 0.0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  using R = Rec<F32>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[NW * NS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* stage0 = smem + (size_t)wid * NS * R::BYTES;
+  // instrumental unknowns (small sets) are gathered from shared memory
+  float2* xi_s = reinterpret_cast<float2*>(smem + (size_t)NW * NS * R::BYTES);
+  if (instr_in_smem) {
+    for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) xi_s[i] = __ldg(x + L.instr_base + i);
+    __syncthreads();
+  }
+  const double4_32a* __restrict__ x3q = reinterpret_cast<const double4_32a*>(x3);
+  uint64_t* bar = bars + wid * NS;
+  const int64_t gw = (int64_t)blockIdx.x * NW + wid, nw = (int64_t)gridDim.x * NW;
+  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
   const double coef = coef_dev ? *coef_dev : coef_host;
+  const ff coef_ff = ff_from_double(coef);
   const bool glob = L.n_glob == 1;
   const ff xg = glob ? ldx(x, L.glob_col) : ff_zero();
-  const int32_t* posv = reinterpret_cast<const int32_t*>(L.att_pos);
-  double nrm = 0.0;
-  int cur_star = -1;
-  ff xa[5];
-#pragma unroll
-  for (int t = 0; t < 5; ++t) xa[t] = ff_zero();
 
-  for (int64_t tile = gwarp; tile < L.n_tiles; tile += nwarps) {
-    const int64_t row0 = tile * TILE_ROWS + lane * ROWS_PER_LANE;
-    const int4 st = __ldcs(L.star + tile * 32 + lane);
-    const int4 sv = __ldcs(L.att_s + tile * 32 + lane);
-    ushort4 ins[6];
+  if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) ins[k] = __ldcs(L.instr + (tile * 6 + k) * 32 + lane);
-    double yo[4];
-    if (row0 + 3 < L.n_rows) {
-      const double2 a = *reinterpret_cast<const double2*>(y + row0);
-      const double2 b = *reinterpret_cast<const double2*>(y + row0 + 2);
-      yo[0] = a.x; yo[1] = a.y; yo[2] = b.x; yo[3] = b.y;
-    } else {
+    for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+    fence_proxy_async();
 #pragma unroll
-      for (int j = 0; j < 4; ++j) yo[j] = (row0 + j < L.n_rows) ? y[row0 + j] : 0.0;
-    }
-    double yn[4];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      ff acc[2] = {ff_zero(), ff_zero()};
-      // astrometric block: 5 consecutive columns of the row's star
-      Vals<F32> va[5];
-#pragma unroll
-      for (int t = 0; t < 5; ++t) va[t].load(L, tile, t, q, lane);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int s = sel4(st, 2 * q + c);
-        if (s != cur_star) {
-          cur_star = s;
-#pragma unroll
-          for (int t = 0; t < 5; ++t) xa[t] = ldx(x, 5 * (int64_t)s + t);
-        }
-#pragma unroll
-        for (int t = 0; t < 5; ++t) acc[c] = ff_add(acc[c], va[t].mul(c, xa[t]));
-      }
-      // attitude: 3 axes x 4 consecutive knots from s_i
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          Vals<F32> v;
-          v.load(L, tile, 5 + 4 * a + i, q, lane);
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int64_t col = L.att_base + (int64_t)a * L.n_knots + sel4(sv, 2 * q + c) + i;
-            acc[c] = ff_add(acc[c], v.mul(c, ldx(x, col)));
-          }
-        }
-      }
-      // instrumental
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        Vals<F32> v;
-        v.load(L, tile, 17 + k, q, lane);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int64_t col = L.instr_base + sel4u(ins[k], 2 * q + c);
-          acc[c] = ff_add(acc[c], v.mul(c, ldx(x, col)));
-        }
-      }
-      if (glob) {
-        Vals<F32> v;
-        v.load(L, tile, 23, q, lane);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) acc[c] = ff_add(acc[c], v.mul(c, xg));
-      }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int j = 2 * q + c;
-        yn[j] = __fma_rn(coef, yo[j], ff_to_double(acc[c]));
-      }
-    }
-    if (row0 + 3 < L.n_rows) {
-      *reinterpret_cast<double2*>(y + row0) = make_double2(yn[0], yn[1]);
-      *reinterpret_cast<double2*>(y + row0 + 2) = make_double2(yn[2], yn[3]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) nrm = __fma_rn(yn[j], yn[j], nrm);
-      if (y_knot) {
-        const int4 p = __ldcs(L.att_pos + tile * 32 + lane);
-        y_knot[p.x] = yn[0];
-        y_knot[p.y] = yn[1];
-        y_knot[p.z] = yn[2];
-        y_knot[p.w] = yn[3];
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (row0 + j < L.n_rows) {
-          y[row0 + j] = yn[j];
-          nrm = __fma_rn(yn[j], yn[j], nrm);
-          if (y_knot) y_knot[posv[row0 + j]] = yn[j];
-        }
+    for (int s = 0; s < NS; ++s) {
+      const int64_t r = gw + s * nw;
+      if (r < L.n_recs) {
+        mbar_expect_tx(&bar[s], R::BYTES);
+        tma_load(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s]);
       }
     }
   }
-  if (norm_out) grid_sum_store(nrm, part, counter, norm_out);
+  __syncwarp();
+
+  ff nrm = ff_zero();
+  double nrm_d = 0.0;
+  uint32_t parity = 0;
+  bool ok = true;
+  int s = 0;
+  for (int64_t r = gw; r < L.n_recs; r += nw) {
+    const unsigned char* rec = stage0 + s * R::BYTES;
+    const int64_t row0 = r * REC_ROWS + 2 * lane;
+    ff yo[2] = {ff_zero(), ff_zero()};
+    double yd[2] = {0.0, 0.0};
+    if constexpr (YFF) {
+      const float2* y = static_cast<const float2*>(yv);
+      if (row0 + 1 < L.n_rows) {
+        const float4 a = *reinterpret_cast<const float4*>(y + row0);
+        yo[0] = ff{a.x, a.y};
+        yo[1] = ff{a.z, a.w};
+      } else if (row0 < L.n_rows) {
+        const float2 a = y[row0];
+        yo[0] = ff{a.x, a.y};
+      }
+    } else {
+      const double* y = static_cast<const double*>(yv);
+      if (row0 + 1 < L.n_rows) {
+        const double2 a = *reinterpret_cast<const double2*>(y + row0);
+        yd[0] = a.x;
+        yd[1] = a.y;
+      } else if (row0 < L.n_rows) {
+        yd[0] = y[row0];
+      }
+    }
+    // bounded, warp-uniform wait for this record
+    bool got = false;
+    for (int i = 0; i < WAIT_LIMIT; ++i)
+      if (__all_sync(0xffffffffu, mbar_try_wait(&bar[s], (parity >> s) & 1u))) {
+        got = true;
+        break;
+      }
+    if (!got) {
+      if (lane == 0) atomicExch(L.err, GSR_E_TIMEOUT);
+      ok = false;
+      break;
+    }
+    parity ^= 1u << s;
+
+    const int2 st = *reinterpret_cast<const int2*>(rec + R::STAR + lane * 8);
+    const int2 sk = *reinterpret_cast<const int2*>(rec + R::ATT_S + lane * 8);
+    const int st_c[2] = {st.x, st.y};
+    const int sk_c[2] = {sk.x, sk.y};
+    ushort2 ik[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      ik[k] = *reinterpret_cast<const ushort2*>(rec + R::INSTR_I + k * 128 + lane * 4);
+
+    // gather x for both rows: astrometric from L2 (lanes share stars), the 12
+    // attitude unknowns as three 32-byte loads from the knot-interleaved copy,
+    // instrumental from shared memory (or L1/L2)
+    ff xv[2][NSLOT];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int t = 0; t < 5; ++t) xv[c][t] = ldx(x, 5 * (int64_t)st_c[c] + t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if constexpr (X3) {
+          const double4_32a q = x3q[(int64_t)sk_c[c] * 3 + a];
+          xv[c][5 + 4 * a + 0] = ff_lo(q.x);
+          xv[c][5 + 4 * a + 1] = ff_lo(q.y);
+          xv[c][5 + 4 * a + 2] = ff_lo(q.z);
+          xv[c][5 + 4 * a + 3] = ff_lo(q.w);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            xv[c][5 + 4 * a + i] = ldx(x, L.att_base + a * L.n_knots + sk_c[c] + i);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int bin = c == 0 ? ik[k].x : ik[k].y;
+        if (instr_in_smem) {
+          const float2 v = xi_s[bin];
+          xv[c][17 + k] = ff{v.x, v.y};
+        } else {
+          xv[c][17 + k] = ldx(x, L.instr_base + bin);
+        }
+      }
+      xv[c][23] = xg;
+    }
+    // six independent accumulation chains per row: astro, 3 attitude axes,
+    // instrumental (+ global), combined by a tree at the end
+    ff part_acc[2][5];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int g = 0; g < 5; ++g) part_acc[c][g] = ff_zero();
+#pragma unroll
+      for (int t = 0; t < NSLOT; ++t) {
+        if (t == 23 && !glob) continue;
+        const int g = t < 5 ? 0 : t < 9 ? 1 : t < 13 ? 2 : t < 17 ? 3 : 4;
+        part_acc[c][g] =
+            ff_add(part_acc[c][g], val_mul<F32>(rec_val<F32>(rec, t, lane, c), xv[c][t]));
+      }
+    }
+    ff acc[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      acc[c] = ff_add(ff_add(ff_add(part_acc[c][0], part_acc[c][1]),
+                             ff_add(part_acc[c][2], part_acc[c][3])),
+                      part_acc[c][4]);
+    const int2 ps = *reinterpret_cast<const int2*>(rec + R::POS + lane * 8);
+    if constexpr (YFF) {
+      float2* y = static_cast<float2*>(yv);
+      ff yn[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) yn[c] = ff_norm(ff_add(ff_mul(coef_ff, yo[c]), acc[c]));
+      if (row0 + 1 < L.n_rows) {
+        *reinterpret_cast<float4*>(y + row0) = make_float4(yn[0].h, yn[0].l, yn[1].h, yn[1].l);
+        nrm = ff_add(nrm, ff_add(ff_mul(yn[0], yn[0]), ff_mul(yn[1], yn[1])));
+        if (y_knot) {
+          y_knot[ps.x] = make_float2(yn[0].h, yn[0].l);
+          y_knot[ps.y] = make_float2(yn[1].h, yn[1].l);
+        }
+      } else if (row0 < L.n_rows) {
+        y[row0] = make_float2(yn[0].h, yn[0].l);
+        nrm = ff_add(nrm, ff_mul(yn[0], yn[0]));
+        if (y_knot) y_knot[ps.x] = make_float2(yn[0].h, yn[0].l);
+      }
+    } else {
+      double* y = static_cast<double*>(yv);
+      const double yn0 = __fma_rn(coef, yd[0], ff_to_double(acc[0]));
+      const double yn1 = __fma_rn(coef, yd[1], ff_to_double(acc[1]));
+      if (row0 + 1 < L.n_rows) {
+        *reinterpret_cast<double2*>(y + row0) = make_double2(yn0, yn1);
+        nrm_d = __fma_rn(yn0, yn0, __fma_rn(yn1, yn1, nrm_d));
+      } else if (row0 < L.n_rows) {
+        y[row0] = yn0;
+        nrm_d = __fma_rn(yn0, yn0, nrm_d);
+      }
+    }
+    // every lane is done with this buffer: refill it with the record NS steps ahead
+    __syncwarp();
+    if (lane == 0) {
+      const int64_t rn = r + NS * nw;
+      if (rn < L.n_recs) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar[s], R::BYTES);
+        tma_load(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s]);
+      }
+    }
+    s = (s + 1 == NS) ? 0 : s + 1;
+  }
+  if (!ok) {
+    // give copies still in flight on this warp's buffers a bounded chance to land
+    for (int q = 0; q < NS; ++q)
+      for (int i = 0; i < WAIT_LIMIT / 16; ++i)
+        if (mbar_try_wait(&bar[q], (parity >> q) & 1u)) break;
+  }
+  if (norm_out) grid_sum_store(YFF ? ff_to_double(nrm) : nrm_d, part, counter, norm_out);
 }
 
 // ---------------------------------------------------------------------------
-// aprod 2, star-ordered part: astrometric (segmented per-star sums over the
-// star-sorted rows, no atomics inside a warp's range), instrumental
-// (shared-memory histogram per block) and global (warp + block sums).
-// Each warp owns a contiguous tile range; runs of one star that cross lanes
-// are joined by a segmented warp scan and runs that cross tiles by a carry.
-// Results are added into x (x += A^T y).
+// aprod 2, astrometric + global part. One warp per record (grid-stride), the
+// two rows of a lane are consecutive; per-star runs are summed in registers,
+// joined across lanes by a segmented inclusive scan and added into x once per
+// record (a star whose rows span records gets one add per record).
 // ---------------------------------------------------------------------------
 struct Astro {
   ff c[5];
 };
-
 __device__ __forceinline__ Astro astro_add(const Astro& a, const Astro& b) {
   Astro r;
 #pragma unroll
   for (int t = 0; t < 5; ++t) r.c[t] = ff_add(a.c[t], b.c[t]);
-  return r;
-}
-__device__ __forceinline__ Astro astro_zero() {
-  Astro r;
-#pragma unroll
-  for (int t = 0; t < 5; ++t) r.c[t] = ff_zero();
   return r;
 }
 __device__ __forceinline__ Astro astro_shfl_up(const Astro& a, int d) {
@@ -263,152 +375,176 @@ __device__ __forceinline__ Astro astro_shfl_up(const Astro& a, int d) {
   for (int t = 0; t < 5; ++t) r.c[t] = ff_shfl_up(a.c[t], d);
   return r;
 }
-__device__ __forceinline__ Astro astro_shfl(const Astro& a, int src) {
-  Astro r;
-#pragma unroll
-  for (int t = 0; t < 5; ++t)
-    r.c[t] = ff{__shfl_sync(0xffffffffu, a.c[t].h, src), __shfl_sync(0xffffffffu, a.c[t].l, src)};
-  return r;
-}
 __device__ __forceinline__ void astro_flush(double* __restrict__ x, int star, const Astro& a) {
 #pragma unroll
-  for (int t = 0; t < 5; ++t) atomicAdd(x + 5 * (int64_t)star + t, ff_to_double(a.c[t]));
+  for (int t = 0; t < 5; ++t) red_ff(x + 5 * (int64_t)star + t, a.c[t]);
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(512) k_aprod2_main(Layout L, const double* __restrict__ y,
-                                                     double* __restrict__ x,
-                                                     const double* stop) {
+__global__ void __launch_bounds__(256) k_aprod2_astro(Layout L, const float2* __restrict__ y,
+                                                      double* __restrict__ x, const double* stop) {
   if (stop && *stop != 0.0) return;
-  extern __shared__ double hist[];  // [n_instr]
+  using R = Rec<F32>;
   const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) hist[i] = 0.0;
-  __syncthreads();
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
   const bool glob = L.n_glob == 1;
   ff gacc = ff_zero();
-  int carry_star = -1;
-  Astro carry = astro_zero();
-  if (gwarp < L.n_main_warps) {
-    const int64_t t_begin = L.row_tile_warp[gwarp], t_end = L.row_tile_warp[gwarp + 1];
-    for (int64_t tile = t_begin; tile < t_end; ++tile) {
-      const int64_t row0 = tile * TILE_ROWS + lane * ROWS_PER_LANE;
-      const int4 st = __ldcs(L.star + tile * 32 + lane);
-      double ud[4];
-      if (row0 + 3 < L.n_rows) {
-        const double2 a = __ldcs(reinterpret_cast<const double2*>(y + row0));
-        const double2 b = __ldcs(reinterpret_cast<const double2*>(y + row0 + 2));
-        ud[0] = a.x; ud[1] = a.y; ud[2] = b.x; ud[3] = b.y;
+  for (int64_t r = gw; r < L.n_recs; r += nw) {
+    const unsigned char* rec = recs + r * R::BYTES;
+    const int64_t row0 = r * REC_ROWS + 2 * lane;
+    // y is padded to whole records (zeros), so the pair load is in bounds
+    const float4 ya = __ldcs(reinterpret_cast<const float4*>(y + row0));
+    const int2 st = __ldcs(reinterpret_cast<const int2*>(rec + R::STAR + lane * 8));
+    ff v[6][2];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      const int slot = t < 5 ? t : 23;
+      if constexpr (F32) {
+        const float2 a =
+            __ldcs(reinterpret_cast<const float2*>(rec + slot_offset<true>(slot) + lane * 8));
+        v[t][0] = ff{a.x, 0.0f};
+        v[t][1] = ff{a.y, 0.0f};
       } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ud[j] = (row0 + j < L.n_rows) ? y[row0 + j] : 0.0;
+        const float4 a =
+            __ldcs(reinterpret_cast<const float4*>(rec + slot_offset<false>(slot) + lane * 16));
+        v[t][0] = ff{a.x, a.y};
+        v[t][1] = ff{a.z, a.w};
       }
-      ff u[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) u[j] = ff_from_double(ud[j]);
-
-      // products of the astrometric slots, per row
-      Astro p[4];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          Vals<F32> v;
-          v.load(L, tile, t, q, lane);
-          p[2 * q].c[t] = v.mul(0, u[2 * q]);
-          p[2 * q + 1].c[t] = v.mul(1, u[2 * q + 1]);
-        }
-      }
-      // global column
-      if (glob) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          Vals<F32> v;
-          v.load(L, tile, 23, q, lane);
-          gacc = ff_add(gacc, v.mul(0, u[2 * q]));
-          gacc = ff_add(gacc, v.mul(1, u[2 * q + 1]));
-        }
-      }
-      // instrumental columns: block-private histogram
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const ushort4 ik = __ldcs(L.instr + (tile * 6 + k) * 32 + lane);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          Vals<F32> v;
-          v.load(L, tile, 17 + k, q, lane);
-          atomicAdd(hist + sel4u(ik, 2 * q), ff_to_double(v.mul(0, u[2 * q])));
-          atomicAdd(hist + sel4u(ik, 2 * q + 1), ff_to_double(v.mul(1, u[2 * q + 1])));
-        }
-      }
-
-      // ---- astrometric segmented reduction ----
-      const int s0 = st.x, s1 = st.y, s2 = st.z, s3 = st.w;
-      const bool uniform = (s0 == s3);
-      // head run: rows with star s0 (a prefix); tail run: rows with star s3 (a suffix)
-      Astro head = p[0];
-      if (s1 == s0) head = astro_add(head, p[1]);
-      if (s2 == s0) head = astro_add(head, p[2]);
-      if (s3 == s0) head = astro_add(head, p[3]);
-      Astro tail;
-      if (uniform) {
-        tail = head;
-      } else {
-        tail = p[3];
-        if (s2 == s3) tail = astro_add(tail, p[2]);
-        if (s1 == s3) tail = astro_add(tail, p[1]);
-        // interior runs (a star strictly inside the lane's four rows)
-        if (s1 != s0 && s1 != s3) {
-          Astro r = p[1];
-          if (s2 == s1) r = astro_add(r, p[2]);
-          astro_flush(x, s1, r);
-        }
-        if (s2 != s0 && s2 != s3 && s2 != s1) astro_flush(x, s2, p[2]);
-      }
-      // the carry from the previous tile joins lane 0's head run or is complete
-      const int first_star = __shfl_sync(0xffffffffu, s0, 0);
-      if (carry_star >= 0 && carry_star != first_star) {
-        if (lane == 0) astro_flush(x, carry_star, carry);
-        carry_star = -1;
-      }
-      if (lane == 0 && carry_star >= 0) {
-        head = astro_add(head, carry);
-        if (uniform) tail = head;
-      }
-      // segmented inclusive scan of the tail runs across lanes
-      const int prev_last = __shfl_up_sync(0xffffffffu, s3, 1);
-      int flag = (lane == 0) || !uniform || (s0 != prev_last);
-      Astro V = tail;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const Astro vu = astro_shfl_up(V, d);
-        const int fu = __shfl_up_sync(0xffffffffu, flag, d);
-        if (lane >= d) {
-          if (!flag) V = astro_add(V, vu);
-          flag |= fu;
-        }
-      }
-      const Astro vprev = astro_shfl_up(V, 1);
-      if (!uniform) {
-        Astro tot = head;
-        if (lane > 0 && s0 == prev_last) tot = astro_add(tot, vprev);
-        astro_flush(x, s0, tot);
-      }
-      const int s0_next = __shfl_down_sync(0xffffffffu, s0, 1);
-      if (lane < 31 && s0_next != s3) astro_flush(x, s3, V);
-      carry_star = __shfl_sync(0xffffffffu, s3, 31);
-      carry = astro_shfl(V, 31);
     }
-    if (carry_star >= 0 && lane == 0) astro_flush(x, carry_star, carry);
+    const ff uf0 = ff{ya.x, ya.y}, uf1 = ff{ya.z, ya.w};
+    Astro p0, p1;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      p0.c[t] = val_mul<F32>(v[t][0], uf0);
+      p1.c[t] = val_mul<F32>(v[t][1], uf1);
+    }
+    if (glob) gacc = ff_add(gacc, ff_add(val_mul<F32>(v[5][0], uf0), val_mul<F32>(v[5][1], uf1)));
+
+    const int s0 = st.x, s1 = st.y;
+    const bool uniform = (s0 == s1);
+    const Astro head = uniform ? astro_add(p0, p1) : p0;
+    const Astro tail = uniform ? head : p1;
+    // segmented inclusive scan of the tail runs across lanes
+    const int prev_last = __shfl_up_sync(0xffffffffu, s1, 1);
+    int flag = (lane == 0) || !uniform || (s0 != prev_last);
+    Astro V = tail;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const Astro vu = astro_shfl_up(V, d);
+      const int fu = __shfl_up_sync(0xffffffffu, flag, d);
+      if (lane >= d) {
+        if (!flag) V = astro_add(V, vu);
+        flag |= fu;
+      }
+    }
+    const Astro vprev = astro_shfl_up(V, 1);
+    if (!uniform) {  // the run of row 0 ends inside this lane
+      Astro tot = head;
+      if (lane > 0 && s0 == prev_last) tot = astro_add(tot, vprev);
+      astro_flush(x, s0, tot);
+    }
+    const int s0_next = __shfl_down_sync(0xffffffffu, s0, 1);
+    if (lane == 31 || s0_next != s1) astro_flush(x, s1, V);
   }
   if (glob) {
     gacc = ff_warp_sum(gacc);
-    if (lane == 0 && (gacc.h != 0.0f || gacc.l != 0.0f)) atomicAdd(x + L.glob_col, ff_to_double(gacc));
+    if (lane == 0) red_ff(x + L.glob_col, gacc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, instrumental part. One block per tile of ct_rows rows (grid-stride).
+// The tile's entries (coefficient, row, bin) are sorted at setup into rounds
+// in which every bin appears at most once; they are TMA-copied into shared
+// memory together with the tile's u, and each round adds its products into
+// the block's float-pair histogram with plain read-modify-write (distinct
+// bins: no conflicts), a barrier separating rounds. The histogram is added
+// into x at the end.
+// ---------------------------------------------------------------------------
+template <bool F32>
+__global__ void __launch_bounds__(512, 1)
+    k_aprod2_instr(Layout L, const float2* __restrict__ y, double* __restrict__ x,
+                   const double* stop) {
+  if (stop && *stop != 0.0) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  constexpr int VB = F32 ? 4 : 8;  // bytes per entry coefficient
+  const int CT = L.ct_rows;
+  // [keys 6*CT u32 | coefficients 6*CT | u pairs CT | histogram n_instr pairs]
+  uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
+  unsigned char* vals = smem + 6 * CT * 4;
+  float2* us = reinterpret_cast<float2*>(vals + 6 * CT * VB);
+  float2* hist = us + CT;
+  for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int64_t ct = blockIdx.x; ct < L.n_ctiles; ct += gridDim.x) {
+    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
+    const int64_t e0 = L.round_entry[k0], e1 = L.round_entry[k1];
+    const int64_t ne = e1 - e0;
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      // sizes rounded up to 16 bytes (the entry arrays are padded for this);
+      // u is padded to whole tiles, so the full tile is always in bounds
+      const uint32_t kb = (uint32_t)((ne * 4 + 15) & ~15LL);
+      const uint32_t vb = (uint32_t)((ne * VB + 15) & ~15LL);
+      const uint32_t ub = (uint32_t)CT * 8u;
+      mbar_expect_tx(&bar, kb + vb + ub);
+      tma_load(us, y + ct * CT, ub, &bar);
+      if (ne > 0) {
+        tma_load(keys, L.ient_key + e0, kb, &bar);
+        if constexpr (F32) tma_load(vals, L.ient_f32 + e0, vb, &bar);
+        else tma_load(vals, L.ient_ff + e0, vb, &bar);
+      }
+    }
+    bool got = false;
+    for (int i = 0; i < WAIT_LIMIT; ++i)
+      if (mbar_try_wait(&bar, parity)) {
+        got = true;
+        break;
+      }
+    if (!__syncthreads_and(got)) {
+      if (threadIdx.x == 0) atomicExch(L.err, GSR_E_TIMEOUT);
+      ok = false;
+      break;
+    }
+    parity ^= 1u;
+    for (int k = k0; k < k1; ++k) {
+      const int a = (int)(L.round_entry[k] - e0), b = (int)(L.round_entry[k + 1] - e0);
+      for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+        const uint32_t key = keys[e];
+        const int row = (int)(key >> INSTR_BIN_BITS);
+        const int bin = (int)(key & ((1u << INSTR_BIN_BITS) - 1));
+        const float2 uu = us[row];
+        ff p;
+        if constexpr (F32) {
+          p = f_mul(reinterpret_cast<const float*>(vals)[e], ff{uu.x, uu.y});
+        } else {
+          const float2 vv = reinterpret_cast<const float2*>(vals)[e];
+          p = ff_mul(ff{vv.x, vv.y}, ff{uu.x, uu.y});
+        }
+        const float2 h = hist[bin];
+        const ff nh = ff_add(ff{h.x, h.y}, p);
+        hist[bin] = make_float2(nh.h, nh.l);
+      }
+      __syncthreads();
+    }
+  }
+  if (!ok) {
+    for (int i = 0; i < WAIT_LIMIT / 16; ++i)
+      if (mbar_try_wait(&bar, parity)) break;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) {
-    const double h = hist[i];
-    if (h != 0.0) atomicAdd(x + L.instr_base + i, h);
+    const float2 h = hist[i];
+    red_ff(x + L.instr_base + i, ff{h.x, h.y});
   }
 }
 
@@ -416,7 +552,8 @@ __global__ void __launch_bounds__(512) k_aprod2_main(Layout L, const double* __r
 // aprod 2, attitude part over the knot-sorted copy: a warp walks its range of
 // start knots; positions with start knot s add into knots s..s+3 of each
 // axis. A sliding 4-knot window per axis lives in registers; knot s is final
-// (for this warp) once bucket s is done and is added into x.
+// (for this warp) once bucket s is done and is added into x. Every load of a
+// step (U positions per lane) is issued before any arithmetic.
 // ---------------------------------------------------------------------------
 template <bool F32>
 __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
@@ -429,7 +566,7 @@ __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const double* __restrict__ y_knot,
+__global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __restrict__ y_knot,
                                                     double* __restrict__ x, const double* stop) {
   if (stop && *stop != 0.0) return;
   const int lane = threadIdx.x & 31;
@@ -443,26 +580,31 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const double* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) win[a][j] = ff_zero();
   const int64_t K = L.n_knots;
+  constexpr int U = 4;  // positions per lane per step
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
     ff acc[12];
 #pragma unroll
     for (int t = 0; t < 12; ++t) acc[t] = ff_zero();
-    int64_t p = p0 + lane;
-    for (; p + 32 < p1; p += 64) {
-      const ff ua = ff_from_double(__ldcs(y_knot + p));
-      const ff ub = ff_from_double(__ldcs(y_knot + p + 32));
+    for (int64_t pb = p0; pb < p1; pb += 32 * U) {
+      ff u[U];
+      ff v[12][U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int64_t p = pb + lane + 32 * q;
+        const bool in = p < p1;
+        const float2 uu = in ? __ldcs(y_knot + p) : make_float2(0.f, 0.f);
+        u[q] = ff{uu.x, uu.y};
+#pragma unroll
+        for (int t = 0; t < 12; ++t) v[t][q] = in ? att_val<F32>(L, t, p) : ff_zero();
+      }
 #pragma unroll
       for (int t = 0; t < 12; ++t) {
-        const ff va = att_val<F32>(L, t, p);
-        const ff vb = att_val<F32>(L, t, p + 32);
-        acc[t] = ff_add(acc[t], ff_add(ff_mul(va, ua), ff_mul(vb, ub)));
-      }
-    }
-    if (p < p1) {
-      const ff ua = ff_from_double(__ldcs(y_knot + p));
+        ff sum = val_mul<F32>(v[t][0], u[0]);
 #pragma unroll
-      for (int t = 0; t < 12; ++t) acc[t] = ff_add(acc[t], ff_mul(att_val<F32>(L, t, p), ua));
+        for (int q = 1; q < U; ++q) sum = ff_add(sum, val_mul<F32>(v[t][q], u[q]));
+        acc[t] = ff_add(acc[t], sum);
+      }
     }
 #pragma unroll
     for (int t = 0; t < 12; ++t) acc[t] = ff_warp_sum(acc[t]);
@@ -473,7 +615,7 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const double* __re
     // knot s is complete for this warp
     if (lane < 3) {
       const ff w0 = lane == 0 ? win[0][0] : lane == 1 ? win[1][0] : win[2][0];
-      atomicAdd(x + L.att_base + lane * K + s, ff_to_double(w0));
+      red_ff(x + L.att_base + lane * K + s, w0);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -488,7 +630,7 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const double* __re
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const ff wj = lane == 0 ? win[0][j] : lane == 1 ? win[1][j] : win[2][j];
-      atomicAdd(x + L.att_base + lane * K + s_end + j, ff_to_double(wj));
+      red_ff(x + L.att_base + lane * K + s_end + j, wj);
     }
   }
 }
@@ -496,7 +638,37 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const double* __re
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+constexpr int A1_NW = 6;                    // warps per aprod 1 block (one block per SM)
+constexpr int A1_NS_FF = 2, A1_NS_F32 = 3;  // record buffers per warp
+constexpr int A1_XI_SMEM_MAX = 6144;        // instrumental unknowns staged in shared memory
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSR_OK : GSR_E_CUDA; }
+
+int set_kernel_attributes() {
+  cudaError_t e = cudaSuccess;
+  auto C = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const int ff_bytes = A1_NW * A1_NS_FF * Rec<false>::BYTES + A1_XI_SMEM_MAX * 8;
+  const int f32_bytes = A1_NW * A1_NS_F32 * Rec<true>::BYTES + A1_XI_SMEM_MAX * 8;
+  C(cudaFuncSetAttribute(k_aprod1<false, true, true, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1<false, false, true, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1<false, false, false, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1<true, true, true, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod1<true, false, true, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod1<true, false, false, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod2_instr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         INSTR_SMEM_BUDGET));
+  C(cudaFuncSetAttribute(k_aprod2_instr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         INSTR_SMEM_BUDGET));
+  return cuda_status(e);
+}
 
 int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, cudaStream_t st) {
   if (n <= 0) return GSR_OK;
@@ -506,67 +678,100 @@ int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, c
   return cuda_status(cudaGetLastError());
 }
 
-int launch_scatter_knot(gsr_system* sys, const double* y, double* y_knot, cudaStream_t st) {
+int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
+                      cudaStream_t st) {
   if (sys->L.n_rows <= 0) return GSR_OK;
   int blocks = (int)((sys->L.n_rows + 255) / 256);
   if (blocks > sys->num_sms * 8) blocks = sys->num_sms * 8;
-  k_scatter_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_knot);
+  k_to_ff_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_ff, y_knot);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_att_x3(gsr_system* sys, const float2* x_ff, const double* stop, cudaStream_t st) {
+  const int64_t n = (sys->L.n_knots - 3) * 12;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sys->num_sms * 4);
+  k_att_x3<<<blocks, 256, 0, st>>>(sys->L, x_ff, sys->S.x3, stop);
+  return cuda_status(cudaGetLastError());
+}
+
+// aprod 1 reads x_ff and its knot-interleaved attitude copy sys->S.x3 (built by
+// launch_att_x3 from the same x_ff beforehand).
+template <bool YFF, bool X3>
+static int launch_aprod1_t(gsr_system* sys, int which_values, const float2* x_ff, void* y,
+                           const double* coef_dev, double coef_host, float2* y_knot,
+                           double* norm_slot, const double* stop, cudaStream_t st) {
+  const Layout& L = sys->L;
+  if (L.n_recs <= 0) {
+    if (norm_slot) return cuda_status(cudaMemsetAsync(norm_slot, 0, sizeof(double), st));
+    return GSR_OK;
+  }
+  int blocks = sys->num_sms;
+  const int64_t need = (L.n_recs + A1_NW - 1) / A1_NW;
+  if (need < blocks) blocks = (int)need;
+  const int xi = L.n_instr <= A1_XI_SMEM_MAX ? 1 : 0;
+  const int xib = xi ? (int)L.n_instr * 8 : 0;
+  if (which_values == GSR_VALUES_F32)
+    k_aprod1<true, YFF, X3, A1_NW, A1_NS_F32>
+        <<<blocks, A1_NW * 32, A1_NW * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
+            L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+            norm_slot, stop, xi);
+  else
+    k_aprod1<false, YFF, X3, A1_NW, A1_NS_FF>
+        <<<blocks, A1_NW * 32, A1_NW * A1_NS_FF * Rec<false>::BYTES + xib, st>>>(
+            L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+            norm_slot, stop, xi);
   return cuda_status(cudaGetLastError());
 }
 
 int launch_aprod1(gsr_system* sys, int which_values, const float2* x_ff, double* y,
                   const double* coef_dev, double coef_host, double* y_knot, double* norm_slot,
                   const double* stop, cudaStream_t st) {
-  const Layout& L = sys->L;
-  if (L.n_tiles <= 0) {
-    if (norm_slot) return cuda_status(cudaMemsetAsync(norm_slot, 0, sizeof(double), st));
-    return GSR_OK;
-  }
-  int blocks = sys->num_sms * 4;
-  const int64_t need = (L.n_tiles + 7) / 8;
-  if (need < blocks) blocks = (int)need;
-  if (which_values == GSR_VALUES_F32)
-    k_aprod1<true><<<blocks, 256, 0, st>>>(L, x_ff, y, coef_dev, coef_host, y_knot, sys->S.red,
-                                           sys->S.count, norm_slot, stop);
-  else
-    k_aprod1<false><<<blocks, 256, 0, st>>>(L, x_ff, y, coef_dev, coef_host, y_knot, sys->S.red,
-                                            sys->S.count, norm_slot, stop);
-  return cuda_status(cudaGetLastError());
+  if (y_knot) return GSR_E_ARG;  // the knot-order copy exists for the float-pair form only
+  return launch_aprod1_t<false, false>(sys, which_values, x_ff, y, coef_dev, coef_host, nullptr,
+                                       norm_slot, stop, st);
 }
 
-int launch_aprod2(gsr_system* sys, int which_values, const double* y, const double* y_knot,
+int launch_aprod1_x3(gsr_system* sys, int which_values, const float2* x_ff, double* y,
+                     cudaStream_t st) {
+  return launch_aprod1_t<false, true>(sys, which_values, x_ff, y, nullptr, 1.0, nullptr, nullptr,
+                                      nullptr, st);
+}
+
+int launch_aprod1_ff(gsr_system* sys, int which_values, const float2* x_ff, float2* y,
+                     const double* coef_dev, float2* y_knot, double* norm_slot,
+                     const double* stop, cudaStream_t st) {
+  return launch_aprod1_t<true, true>(sys, which_values, x_ff, y, coef_dev, 0.0, y_knot, norm_slot,
+                                     stop, st);
+}
+
+int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const float2* y_knot,
                   double* x, const double* stop, cudaStream_t st) {
   const Layout& L = sys->L;
   if (L.n_rows <= 0) return GSR_OK;
-  cudaError_t e;
-  // attitude part on the side stream, concurrent with the star-ordered part
-  if ((e = cudaEventRecord(sys->ev_fork, st)) != cudaSuccess) return GSR_E_CUDA;
-  if ((e = cudaStreamWaitEvent(sys->side, sys->ev_fork, 0)) != cudaSuccess) return GSR_E_CUDA;
+  const bool f32 = which_values == GSR_VALUES_F32;
+  // attitude part on the side stream, concurrent with the star-ordered parts
+  if (cudaEventRecord(sys->ev_fork, st) != cudaSuccess) return GSR_E_CUDA;
+  if (cudaStreamWaitEvent(sys->side, sys->ev_fork, 0) != cudaSuccess) return GSR_E_CUDA;
   const int att_blocks = (L.n_att_warps + 7) / 8;
   if (att_blocks > 0) {
-    if (which_values == GSR_VALUES_F32)
-      k_aprod2_att<true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
-    else
-      k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
-    if ((e = cudaGetLastError()) != cudaSuccess) return GSR_E_CUDA;
+    if (f32) k_aprod2_att<true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
-  if (which_values == GSR_VALUES_F32)
-    k_aprod2_main<true><<<sys->main_ctas, sys->main_block, sys->hist_bytes, st>>>(L, y, x, stop);
-  else
-    k_aprod2_main<false><<<sys->main_ctas, sys->main_block, sys->hist_bytes, st>>>(L, y, x, stop);
-  if ((e = cudaGetLastError()) != cudaSuccess) return GSR_E_CUDA;
-  if ((e = cudaEventRecord(sys->ev_join, sys->side)) != cudaSuccess) return GSR_E_CUDA;
-  if ((e = cudaStreamWaitEvent(st, sys->ev_join, 0)) != cudaSuccess) return GSR_E_CUDA;
+  const int ib = (int)std::min<int64_t>(sys->num_sms, L.n_ctiles);
+  const int ismem = (int)instr_smem_bytes(L.ct_rows, L.n_instr, f32);
+  if (ib > 0) {
+    if (f32) k_aprod2_instr<true><<<ib, 512, ismem, st>>>(L, y, x, stop);
+    else k_aprod2_instr<false><<<ib, 512, ismem, st>>>(L, y, x, stop);
+    if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  }
+  const int ab = (int)std::min<int64_t>((int64_t)sys->num_sms * 8, (L.n_recs + 7) / 8);
+  if (f32) k_aprod2_astro<true><<<ab, 256, 0, st>>>(L, y, x, stop);
+  else k_aprod2_astro<false><<<ab, 256, 0, st>>>(L, y, x, stop);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  if (cudaEventRecord(sys->ev_join, sys->side) != cudaSuccess) return GSR_E_CUDA;
+  if (cudaStreamWaitEvent(st, sys->ev_join, 0) != cudaSuccess) return GSR_E_CUDA;
   return GSR_OK;
-}
-
-int set_kernel_attributes(int hist_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_aprod2_main<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, hist_bytes);
-  if (e != cudaSuccess) return GSR_E_CUDA;
-  e = cudaFuncSetAttribute(k_aprod2_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           hist_bytes);
-  return cuda_status(e);
 }
 
 }  // namespace gsr

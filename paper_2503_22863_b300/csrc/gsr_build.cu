@@ -1,14 +1,14 @@
 // gsr_create / gsr_destroy and the plain aprod entry points.
 //
 // gsr_create validates the packed rows of Sec. 2 on the host (one pass,
-// several threads), builds the small index structures (star-sorted warp
-// ranges, the counting sort of rows by attitude start knot), uploads the
-// values in chunks and lays them out on the device as float pairs in
-// coalesced warp tiles, plus a knot-ordered copy of the attitude block. The
-// column norms ||A_:,j|| (used by the column-scaling preconditioner, Sec. 2
-// solver step 2) are computed on the device.
+// several threads), builds the index structures (the stable counting sort of
+// rows by attitude start knot, the attitude warp ranges, and the instrumental
+// entries of every tile ordered into rounds of distinct bins), uploads the
+// values in chunks and lays them out on the device as 64-row records of float
+// pairs (plus an optional FP32 copy) and a knot-ordered copy of the attitude
+// block. The column norms ||A_:,j|| (used by the column-scaling preconditioner,
+// Sec. 2 solver step 2) are computed on the device.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -22,43 +22,55 @@ namespace gsr {
 namespace {
 
 constexpr int64_t CHUNK_ROWS = 1 << 22;  // rows per upload chunk (768 MB of values)
-constexpr int MAX_HIST_INSTR = 28672;    // instrumental bins that fit a block's shared memory
 
-__global__ void k_layout(Layout L, float* __restrict__ vals_ff, float* __restrict__ vals_f32,
-                         float2* __restrict__ att_ff, float* __restrict__ att_f32,
-                         uint16_t* __restrict__ instr_t, const double* __restrict__ raw,
+template <bool F32>
+__device__ __forceinline__ void put_indices(unsigned char* rec, int l, int c, int star, int s,
+                                            int p, const int32_t* ins) {
+  using R = Rec<F32>;
+  reinterpret_cast<int32_t*>(rec + R::STAR)[2 * l + c] = star;
+  reinterpret_cast<int32_t*>(rec + R::ATT_S)[2 * l + c] = s;
+  reinterpret_cast<int32_t*>(rec + R::POS)[2 * l + c] = p;
+  for (int k = 0; k < 6; ++k)
+    reinterpret_cast<uint16_t*>(rec + R::INSTR_I + k * 128)[2 * l + c] = (uint16_t)ins[k];
+}
+
+// Lay out rows [r0, r0+n) of the raw upload into the records and the
+// knot-ordered attitude copy; accumulate the squared column norms.
+__global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
+                         unsigned char* __restrict__ rec_f32, float2* __restrict__ att_ff,
+                         float* __restrict__ att_f32, const double* __restrict__ raw,
                          const int32_t* __restrict__ raw_instr, const int32_t* __restrict__ star,
-                         const int32_t* __restrict__ s_knot, const int32_t* __restrict__ pos,
-                         double* __restrict__ c2, int64_t r0, int64_t n) {
+                         const int32_t* __restrict__ s_knot, double* __restrict__ c2, int64_t r0,
+                         int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = r0 + i;
-    const int64_t tile = r / TILE_ROWS;
-    const int l = (int)((r % TILE_ROWS) / ROWS_PER_LANE);
-    const int j = (int)(r % ROWS_PER_LANE);
-    const int q = j >> 1, c = j & 1;
-    const int64_t st = star[r], sk = s_knot[r], p = pos[r];
+    const int64_t rec = r / REC_ROWS;
+    const int l = (int)((r % REC_ROWS) >> 1), c = (int)(r & 1);
+    const int st = star[r], sk = s_knot[r], p = L.pos[r];
+    unsigned char* rf = rec_ff + rec * Rec<false>::BYTES;
+    unsigned char* r32 = rec_f32 ? rec_f32 + rec * Rec<true>::BYTES : nullptr;
+    put_indices<false>(rf, l, c, st, sk, p, raw_instr + i * 6);
+    if (r32) put_indices<true>(r32, l, c, st, sk, p, raw_instr + i * 6);
     for (int t = 0; t < NSLOT; ++t) {
       double v = raw[i * NSLOT + t];
       if (t == 23 && L.n_glob == 0) v = 0.0;
       const float h = __double2float_rn(v);
       const float lo = __double2float_rn(v - (double)h);
-      const int64_t e = ((tile * NSLOT + t) * 2 + q) * 32 + l;
-      vals_ff[e * 4 + 2 * c] = h;
-      vals_ff[e * 4 + 2 * c + 1] = lo;
-      if (vals_f32) vals_f32[e * 2 + c] = h;
+      float* pf = reinterpret_cast<float*>(rf + slot_offset<false>(t) + l * 16);
+      pf[2 * c] = h;
+      pf[2 * c + 1] = lo;
+      if (r32) reinterpret_cast<float*>(r32 + slot_offset<true>(t) + l * 8)[c] = h;
       int64_t col;
       if (t < 5) {
-        col = 5 * st + t;
+        col = 5 * (int64_t)st + t;
       } else if (t < 17) {
         const int a = (t - 5) >> 2, jj = (t - 5) & 3;
         col = L.att_base + a * L.n_knots + sk + jj;
         att_ff[(int64_t)(t - 5) * L.n_rows + p] = make_float2(h, lo);
         if (att_f32) att_f32[(int64_t)(t - 5) * L.n_rows + p] = h;
       } else if (t < 23) {
-        const int idx = raw_instr[i * 6 + (t - 17)];
-        col = L.instr_base + idx;
-        instr_t[((tile * 6 + (t - 17)) * 32 + l) * 4 + j] = (uint16_t)idx;
+        col = L.instr_base + raw_instr[i * 6 + (t - 17)];
       } else {
         if (L.n_glob == 0) continue;
         col = L.glob_col;
@@ -66,6 +78,17 @@ __global__ void k_layout(Layout L, float* __restrict__ vals_ff, float* __restric
       atomicAdd(c2 + col, v * v);
     }
   }
+}
+
+// Padding rows of the last record: the last real star, knot 0, zero values.
+__global__ void k_pad_records(Layout L, unsigned char* rec_ff, unsigned char* rec_f32, int star) {
+  const int64_t r = L.n_rows + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= L.n_recs * REC_ROWS) return;
+  const int64_t rec = r / REC_ROWS;
+  const int l = (int)((r % REC_ROWS) >> 1), c = (int)(r & 1);
+  const int32_t zeros[6] = {0, 1, 2, 3, 4, 5};
+  put_indices<false>(rec_ff + rec * Rec<false>::BYTES, l, c, star, 0, 0, zeros);
+  if (rec_f32) put_indices<true>(rec_f32 + rec * Rec<true>::BYTES, l, c, star, 0, 0, zeros);
 }
 
 __global__ void k_sqrt(double* __restrict__ a, int64_t n) {
@@ -89,10 +112,11 @@ int dalloc(T** p, size_t count) {
 
 void free_system(gsr_system* s) {
   if (!s) return;
-  void* ptrs[] = {s->vals_ff, s->vals_f32, s->star, s->att_s, s->att_pos, s->instr,
-                  s->att_knot_ff, s->att_knot_f32, s->knot_start, s->att_warp_knot,
-                  s->row_tile_warp, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
-                  s->dscale, s->v_ff, s->scal, s->S.red, s->S.count, s->S.x_ff, s->S.y_knot};
+  void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
+                  s->att_warp_knot, s->ct_round, s->round_entry, s->ient_ff, s->ient_f32,
+                  s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
+                  s->dscale, s->v_ff, s->scal, s->S.red, s->S.count, s->S.x_ff, s->S.x3,
+                  s->S.y_ff, s->S.y_knot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->host_scal) cudaFreeHost(s->host_scal);
@@ -129,6 +153,92 @@ int validate_rows(const gsr_dims& d, const double* vals, const int64_t* astro_of
   return GSR_OK;
 }
 
+template <typename F>
+void parallel_for(int64_t n, unsigned nt, F f) {
+  if (nt <= 1 || n < 2) {
+    for (int64_t i = 0; i < n; ++i) f(i, 0u);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nt; ++k)
+    th.emplace_back([&, k] {
+      for (int64_t i = k; i < n; i += nt) f(i, k);
+    });
+  for (auto& t : th) t.join();
+}
+
+// Instrumental entries of every tile of ct rows, ordered into rounds in which
+// each bin occurs at most once (round = earlier occurrences of the bin in the
+// tile), and by bin inside a round.
+struct InstrRounds {
+  std::vector<int32_t> ct_round;
+  std::vector<int64_t> round_entry;
+  std::vector<uint32_t> key;
+  std::vector<float2> vff;
+  std::vector<float> vf32;
+};
+
+void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* instr, int ct,
+                        bool want_f32, unsigned nt, InstrRounds& out) {
+  const int64_t n = d.n_rows;
+  const int64_t n_ct = (n + ct - 1) / ct;
+  std::vector<int32_t> rounds(n_ct, 0);
+  std::vector<std::vector<int32_t>> occ(nt, std::vector<int32_t>(d.n_instr, 0));
+  parallel_for(n_ct, nt, [&](int64_t t, unsigned w) {
+    auto& o = occ[w];
+    const int64_t a = t * ct, b = std::min<int64_t>(n, a + ct);
+    int mx = 0;
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 6; ++k) mx = std::max(mx, ++o[instr[i * 6 + k]]);
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
+    rounds[t] = mx;
+  });
+  out.ct_round.assign(n_ct + 1, 0);
+  for (int64_t t = 0; t < n_ct; ++t) out.ct_round[t + 1] = out.ct_round[t] + rounds[t];
+  const int64_t n_rounds = out.ct_round[n_ct];
+  const int64_t n_ent = 6 * n;
+  out.round_entry.assign(n_rounds + 1, n_ent);
+  out.key.assign(n_ent + 4, 0u);  // +4: TMA copies are rounded up to 16 bytes
+  out.vff.assign(n_ent + 4, make_float2(0.f, 0.f));
+  if (want_f32) out.vf32.assign(n_ent + 4, 0.f);
+  parallel_for(n_ct, nt, [&](int64_t t, unsigned w) {
+    auto& o = occ[w];
+    const int64_t a = t * ct, b = std::min<int64_t>(n, a + ct);
+    std::vector<uint64_t> order;
+    order.reserve(6 * (b - a));
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 6; ++k) {
+        const int bin = instr[i * 6 + k];
+        const uint64_t rnd = (uint64_t)o[bin]++;
+        order.push_back((rnd << 40) | ((uint64_t)bin << 24) | ((uint64_t)(i - a) << 3) |
+                        (uint64_t)k);
+      }
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
+    std::sort(order.begin(), order.end());
+    int64_t e = 6 * a;
+    int64_t kr = out.ct_round[t];
+    int64_t cur = -1;
+    for (uint64_t v : order) {
+      const int64_t rnd = (int64_t)(v >> 40);
+      const uint32_t bin = (uint32_t)((v >> 24) & 0xffff);
+      const int64_t row = (int64_t)((v >> 3) & 0x1fffff);
+      const int k = (int)(v & 7);
+      if (rnd != cur) {
+        out.round_entry[kr + rnd] = e;
+        cur = rnd;
+      }
+      out.key[e] = ((uint32_t)row << INSTR_BIN_BITS) | bin;
+      const double x = vals[(a + row) * NSLOT + 17 + k];
+      const float h = (float)x;
+      out.vff[e] = make_float2(h, (float)(x - (double)h));
+      if (want_f32) out.vf32[e] = h;
+      ++e;
+    }
+  });
+}
+
 }  // namespace
 
 int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_off,
@@ -145,15 +255,17 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   if (d.n_rows >= (int64_t(1) << 31) || n_unk >= (int64_t(1) << 31) ||
       d.n_instr > MAX_HIST_INSTR)
     return GSR_E_UNSUPPORTED;
+  const bool want_f32 = d.storage == GSR_STORE_F32_PLUS_F64;
+
   const int64_t n = d.n_rows;
-  const int64_t n_tiles = (n + TILE_ROWS - 1) / TILE_ROWS;
-  const int64_t n_pad = n_tiles * TILE_ROWS;
+  const int64_t n_recs = (n + REC_ROWS - 1) / REC_ROWS;
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 100000) nt = 1;
 
   // ---- host validation and per-row indices (multi-threaded) ----
-  std::vector<int32_t> star(n_pad), s_knot(n_pad), pos(n_pad);
+  std::vector<int32_t> star(std::max<int64_t>(n, 1)), s_knot(std::max<int64_t>(n, 1)),
+      pos(std::max<int64_t>(n, 1));
   {
-    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    if (n < 100000) nt = 1;
     std::vector<int> rc(nt, GSR_OK);
     std::vector<std::thread> th;
     const int64_t per = (n + nt - 1) / nt;
@@ -168,12 +280,6 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     for (int r : rc)
       if (r != GSR_OK) return r;
   }
-  // padded rows: same star as the last row, knot 0, zero values
-  for (int64_t r = n; r < n_pad; ++r) {
-    star[r] = n > 0 ? star[n - 1] : 0;
-    s_knot[r] = 0;
-    pos[r] = 0;
-  }
   // ---- counting sort of rows by start knot (stable) ----
   const int64_t n_buckets = d.n_knots - 3;
   std::vector<int64_t> knot_start(n_buckets + 1, 0);
@@ -183,6 +289,11 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     std::vector<int64_t> next(knot_start.begin(), knot_start.end() - 1);
     for (int64_t r = 0; r < n; ++r) pos[r] = (int32_t)(next[s_knot[r]]++);
   }
+  // ---- instrumental tiles: the largest that fits the kernel's shared memory ----
+  int ct = CT_ROWS_MAX;
+  while (ct > REC_ROWS && instr_smem_bytes(ct, d.n_instr, false) > INSTR_SMEM_BUDGET) ct >>= 1;
+  InstrRounds ir;
+  build_instr_rounds(d, vals, instr, ct, want_f32, nt, ir);
 
   // host validation is done; everything below needs the device
   if (cudaSetDevice(device) != cudaSuccess) return GSR_E_CUDA;
@@ -201,22 +312,14 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.n_instr = d.n_instr;
   L.n_glob = d.n_glob;
   L.n_unk = n_unk;
-  L.n_tiles = n_tiles;
+  L.n_recs = n_recs;
   L.att_base = 5 * d.n_stars;
   L.instr_base = L.att_base + 3 * d.n_knots;
   L.glob_col = L.instr_base + d.n_instr;
+  L.ct_rows = ct;
+  L.n_ctiles = (int64_t)ir.ct_round.size() - 1;
 
-  // ---- launch shapes and warp partitions ----
-  sys->hist_bytes = (int)(d.n_instr * sizeof(double));
-  sys->main_block = 512;
-  // one 512-thread block per SM: the kernel needs ~110 registers per thread
-  const int per_sm = 1;
-  sys->main_ctas = sys->num_sms * per_sm;
-  L.n_main_warps = sys->main_ctas * (sys->main_block / 32);
-  std::vector<int64_t> row_tile_warp(L.n_main_warps + 1);
-  for (int w = 0; w <= L.n_main_warps; ++w)
-    row_tile_warp[w] = (n_tiles * (int64_t)w) / L.n_main_warps;
-  L.n_att_warps = sys->num_sms * 16;
+  L.n_att_warps = sys->num_sms * 8;  // one 8-warp block per SM (the kernel holds ~180 registers)
   std::vector<int32_t> att_warp_knot(L.n_att_warps + 1);
   {
     int64_t b = 0;
@@ -230,25 +333,31 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   }
 
   // ---- device allocations ----
+  const size_t n_ent = ir.key.size();
+  const size_t n_rounds = ir.round_entry.size();
   int rc = GSR_OK;
   auto A = [&](int r) {
     if (rc == GSR_OK) rc = r;
   };
-  A(dalloc(&sys->vals_ff, (size_t)n_pad * NSLOT / 2));  // float4 per 2 rows per slot
-  if (d.storage == GSR_STORE_F32_PLUS_F64) A(dalloc(&sys->vals_f32, (size_t)n_pad * NSLOT / 2 + 1));
-  A(dalloc(&sys->star, (size_t)n_pad / 4 + 1));
-  A(dalloc(&sys->att_s, (size_t)n_pad / 4 + 1));
-  A(dalloc(&sys->att_pos, (size_t)n_pad / 4 + 1));
-  A(dalloc(&sys->instr, (size_t)n_pad * 6 / 4 + 1));
+  A(dalloc(&sys->rec_ff, (size_t)n_recs * Rec<false>::BYTES));
+  if (want_f32) A(dalloc(&sys->rec_f32, (size_t)n_recs * Rec<true>::BYTES));
+  A(dalloc(&sys->pos, (size_t)n));
   A(dalloc(&sys->att_knot_ff, (size_t)n * 12));
-  if (d.storage == GSR_STORE_F32_PLUS_F64) A(dalloc(&sys->att_knot_f32, (size_t)n * 12));
+  if (want_f32) A(dalloc(&sys->att_knot_f32, (size_t)n * 12));
   A(dalloc(&sys->knot_start, (size_t)n_buckets + 1));
   A(dalloc(&sys->att_warp_knot, (size_t)L.n_att_warps + 1));
-  A(dalloc(&sys->row_tile_warp, (size_t)L.n_main_warps + 1));
+  A(dalloc(&sys->ct_round, ir.ct_round.size()));
+  A(dalloc(&sys->round_entry, n_rounds));
+  A(dalloc(&sys->ient_key, n_ent));
+  A(dalloc(&sys->ient_ff, n_ent));
+  if (want_f32) A(dalloc(&sys->ient_f32, n_ent));
+  A(dalloc(&sys->err, 1));
   A(dalloc(&sys->colnorm, (size_t)n_unk));
   A(dalloc(&sys->S.red, 65536));
   A(dalloc(&sys->S.count, 64));
   A(dalloc(&sys->S.x_ff, (size_t)n_unk));
+  A(dalloc(&sys->S.x3, (size_t)n_buckets * 12));
+  A(dalloc(&sys->S.y_ff, (size_t)padded_rows(L)));
   A(dalloc(&sys->S.y_knot, (size_t)n));
   if (rc != GSR_OK) {
     free_system(sys);
@@ -270,70 +379,88 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   auto C = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
-  C(cudaMemsetAsync(sys->vals_ff, 0, (size_t)n_pad * NSLOT * sizeof(float4) / 2, st));
-  if (sys->vals_f32) C(cudaMemsetAsync(sys->vals_f32, 0, (size_t)n_pad * NSLOT * sizeof(float), st));
-  C(cudaMemsetAsync(sys->instr, 0, (size_t)n_pad * 6 * sizeof(uint16_t), st));
+  C(cudaMemsetAsync(sys->rec_ff, 0, (size_t)n_recs * Rec<false>::BYTES, st));
+  if (want_f32) C(cudaMemsetAsync(sys->rec_f32, 0, (size_t)n_recs * Rec<true>::BYTES, st));
   C(cudaMemsetAsync(sys->S.count, 0, 64 * sizeof(unsigned int), st));
+  C(cudaMemsetAsync(sys->err, 0, sizeof(int), st));
   C(cudaMemsetAsync(sys->colnorm, 0, (size_t)n_unk * sizeof(double), st));
-  C(cudaMemcpyAsync(sys->star, star.data(), (size_t)n_pad * 4, cudaMemcpyHostToDevice, st));
-  C(cudaMemcpyAsync(sys->att_s, s_knot.data(), (size_t)n_pad * 4, cudaMemcpyHostToDevice, st));
-  C(cudaMemcpyAsync(sys->att_pos, pos.data(), (size_t)n_pad * 4, cudaMemcpyHostToDevice, st));
+  C(cudaMemsetAsync(sys->S.y_ff, 0, (size_t)padded_rows(L) * sizeof(float2), st));
+  C(cudaMemcpyAsync(sys->pos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->knot_start, knot_start.data(), (size_t)(n_buckets + 1) * 8,
                     cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->att_warp_knot, att_warp_knot.data(), (size_t)(L.n_att_warps + 1) * 4,
                     cudaMemcpyHostToDevice, st));
-  C(cudaMemcpyAsync(sys->row_tile_warp, row_tile_warp.data(), (size_t)(L.n_main_warps + 1) * 8,
+  C(cudaMemcpyAsync(sys->ct_round, ir.ct_round.data(), ir.ct_round.size() * 4,
                     cudaMemcpyHostToDevice, st));
+  C(cudaMemcpyAsync(sys->round_entry, ir.round_entry.data(), n_rounds * 8,
+                    cudaMemcpyHostToDevice, st));
+  C(cudaMemcpyAsync(sys->ient_key, ir.key.data(), n_ent * 4, cudaMemcpyHostToDevice, st));
+  C(cudaMemcpyAsync(sys->ient_ff, ir.vff.data(), n_ent * 8, cudaMemcpyHostToDevice, st));
+  if (want_f32)
+    C(cudaMemcpyAsync(sys->ient_f32, ir.vf32.data(), n_ent * 4, cudaMemcpyHostToDevice, st));
   if (e != cudaSuccess) return fail(GSR_E_CUDA);
 
-  L.vals_ff = sys->vals_ff;
-  L.vals_f32 = sys->vals_f32;
-  L.star = sys->star;
-  L.att_s = sys->att_s;
-  L.att_pos = sys->att_pos;
-  L.instr = sys->instr;
+  L.rec_ff = sys->rec_ff;
+  L.rec_f32 = sys->rec_f32;
+  L.pos = sys->pos;
   L.att_knot_ff = sys->att_knot_ff;
   L.att_knot_f32 = sys->att_knot_f32;
   L.knot_start = sys->knot_start;
   L.att_warp_knot = sys->att_warp_knot;
-  L.row_tile_warp = sys->row_tile_warp;
+  L.ct_round = sys->ct_round;
+  L.round_entry = sys->round_entry;
+  L.ient_ff = sys->ient_ff;
+  L.ient_f32 = sys->ient_f32;
+  L.ient_key = sys->ient_key;
+  L.err = sys->err;
 
-  // ---- chunked upload of the values and instrumental indices ----
+  // ---- chunked upload of the values and indices, laid out on the device ----
   if (n > 0) {
     const int64_t ch = std::min<int64_t>(CHUNK_ROWS, n);
     double* raw = nullptr;
     int32_t* raw_instr = nullptr;
+    int32_t* d_star = nullptr;
+    int32_t* d_sk = nullptr;
     int r1 = dalloc(&raw, (size_t)ch * NSLOT);
     int r2 = dalloc(&raw_instr, (size_t)ch * 6);
-    if (r1 != GSR_OK || r2 != GSR_OK) {
+    int r3 = dalloc(&d_star, (size_t)n);
+    int r4 = dalloc(&d_sk, (size_t)n);
+    if (r1 != GSR_OK || r2 != GSR_OK || r3 != GSR_OK || r4 != GSR_OK) {
       if (raw) cudaFree(raw);
       if (raw_instr) cudaFree(raw_instr);
-      return fail(r1 != GSR_OK ? r1 : r2);
+      if (d_star) cudaFree(d_star);
+      if (d_sk) cudaFree(d_sk);
+      return fail(r1 != GSR_OK ? r1 : r2 != GSR_OK ? r2 : r3 != GSR_OK ? r3 : r4);
     }
+    C(cudaMemcpyAsync(d_star, star.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    C(cudaMemcpyAsync(d_sk, s_knot.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
     for (int64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += ch) {
       const int64_t m = std::min(ch, n - r0);
       C(cudaMemcpyAsync(raw, vals + r0 * NSLOT, (size_t)m * NSLOT * 8, cudaMemcpyHostToDevice, st));
       C(cudaMemcpyAsync(raw_instr, instr + r0 * 6, (size_t)m * 6 * 4, cudaMemcpyHostToDevice, st));
-      int blocks = (int)std::min<int64_t>((m + 255) / 256, sys->num_sms * 16);
-      k_layout<<<blocks, 256, 0, st>>>(L, reinterpret_cast<float*>(sys->vals_ff),
-                                       reinterpret_cast<float*>(sys->vals_f32), sys->att_knot_ff,
-                                       sys->att_knot_f32, reinterpret_cast<uint16_t*>(sys->instr),
-                                       raw, raw_instr, reinterpret_cast<const int32_t*>(sys->star),
-                                       reinterpret_cast<const int32_t*>(sys->att_s),
-                                       reinterpret_cast<const int32_t*>(sys->att_pos),
+      const int blocks = (int)std::min<int64_t>((m + 255) / 256, sys->num_sms * 16);
+      k_layout<<<blocks, 256, 0, st>>>(L, sys->rec_ff, sys->rec_f32, sys->att_knot_ff,
+                                       sys->att_knot_f32, raw, raw_instr, d_star, d_sk,
                                        sys->colnorm, r0, m);
+      C(cudaGetLastError());
+    }
+    const int64_t n_pad = n_recs * REC_ROWS - n;
+    if (n_pad > 0) {
+      k_pad_records<<<(int)((n_pad + 255) / 256), 256, 0, st>>>(L, sys->rec_ff, sys->rec_f32,
+                                                                star[n - 1]);
       C(cudaGetLastError());
     }
     C(cudaStreamSynchronize(st));
     cudaFree(raw);
     cudaFree(raw_instr);
+    cudaFree(d_star);
+    cudaFree(d_sk);
   }
   k_sqrt<<<sys->num_sms * 4, 256, 0, st>>>(sys->colnorm, n_unk);
   C(cudaGetLastError());
   C(cudaStreamSynchronize(st));
   if (e != cudaSuccess) return fail(GSR_E_CUDA);
-  if (set_kernel_attributes(MAX_HIST_INSTR * (int)sizeof(double)) != GSR_OK) return fail(GSR_E_CUDA);
-
+  if (set_kernel_attributes() != GSR_OK) return fail(GSR_E_CUDA);
   *out = sys;
   return GSR_OK;
 }
@@ -385,25 +512,26 @@ int gsr_aprod1_values(gsr_system* sys, int which_values, const double* x, double
                       void* stream) {
   if (!sys || (!x && sys->L.n_unk > 0) || (!y && sys->L.n_rows > 0)) return GSR_E_ARG;
   if (which_values != GSR_VALUES_F64 && which_values != GSR_VALUES_F32) return GSR_E_ARG;
-  if (which_values == GSR_VALUES_F32 && !sys->vals_f32) return GSR_E_ARG;
+  if (which_values == GSR_VALUES_F32 && !sys->rec_f32) return GSR_E_ARG;
   if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = gsr::launch_to_ff(x, nullptr, sys->S.x_ff, sys->L.n_unk, st);
   if (rc != GSR_OK) return rc;
-  return gsr::launch_aprod1(sys, which_values, sys->S.x_ff, y, nullptr, 1.0, nullptr, nullptr,
-                            nullptr, st);
+  rc = gsr::launch_att_x3(sys, sys->S.x_ff, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  return gsr::launch_aprod1_x3(sys, which_values, sys->S.x_ff, y, st);
 }
 
 int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double* x,
                       void* stream) {
   if (!sys || (!x && sys->L.n_unk > 0) || (!y && sys->L.n_rows > 0)) return GSR_E_ARG;
   if (which_values != GSR_VALUES_F64 && which_values != GSR_VALUES_F32) return GSR_E_ARG;
-  if (which_values == GSR_VALUES_F32 && !sys->vals_f32) return GSR_E_ARG;
+  if (which_values == GSR_VALUES_F32 && !sys->rec_f32) return GSR_E_ARG;
   if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = gsr::launch_scatter_knot(sys, y, sys->S.y_knot, st);
+  int rc = gsr::launch_to_ff_knot(sys, y, sys->S.y_ff, sys->S.y_knot, st);
   if (rc != GSR_OK) return rc;
-  return gsr::launch_aprod2(sys, which_values, y, sys->S.y_knot, x, nullptr, st);
+  return gsr::launch_aprod2(sys, which_values, sys->S.y_ff, sys->S.y_knot, x, nullptr, st);
 }
 
 int gsr_aprod1(gsr_system* sys, const double* x, double* y, void* stream) {

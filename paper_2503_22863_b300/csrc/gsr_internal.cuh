@@ -1,5 +1,5 @@
 // Internal definitions of libgsr: device layout of a system, float-pair
-// arithmetic and launch helpers. Not part of the public ABI.
+// arithmetic, TMA / mbarrier helpers and launch helpers. Not part of the ABI.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -9,9 +9,63 @@
 namespace gsr {
 
 constexpr int NSLOT = 24;
-constexpr int ROWS_PER_LANE = 4;                 // R consecutive rows per thread
-constexpr int TILE_ROWS = 32 * ROWS_PER_LANE;    // rows per warp tile
+constexpr int REC_ROWS = 64;        // rows per record; lane l owns rows 2l, 2l+1
+constexpr int CT_ROWS_MAX = 2048;   // rows per instrumental tile (at most)
 constexpr int NUM_SMS_B300 = 148;
+constexpr int MAX_HIST_INSTR = 24576;  // instrumental bins of one block's histogram
+constexpr int INSTR_BIN_BITS = 15;     // bin field of an instrumental entry key
+constexpr int INSTR_SMEM_BUDGET = 220 * 1024;  // dynamic shared memory of the instr kernel
+
+// Shared memory of the instrumental kernel for a tile of ct_rows rows:
+// keys (4 B) and coefficients (8 B pair / 4 B FP32) of 6 entries per row,
+// u of the tile as pairs (8 B per row) and the float-pair histogram.
+__host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t n_instr,
+                                                       bool f32) {
+  return 6 * ct_rows * 4 + 6 * ct_rows * (f32 ? 4 : 8) + ct_rows * 8 + n_instr * 8;
+}
+
+// ---------------------------------------------------------------------------
+// Row records. One record = 64 consecutive rows, everything aprod 1 needs for
+// them in one contiguous block (one TMA bulk copy). Per-slot chunks hold the
+// two rows of each lane side by side. Byte offsets inside a record:
+//   float pairs (REC_FF bytes)            FP32 copy (REC_F32 bytes)
+//   slots 0-4       float4[5][32]  0      float2[5][32]   0
+//   slot 23 (glob)  float4[32]     2560   float2[32]      1280
+//   star            int2[32]       3072                   1536
+//   slots 17-22     float4[6][32]  3328   float2[6][32]   1792
+//   instr index     ushort2[6][32] 6400                   3328
+//   slots 5-16      float4[12][32] 7168   float2[12][32]  4096
+//   start knot s    int2[32]       13312                  7168
+//   knot position   int2[32]       13568                  7424
+// The star-ordered part of aprod 2 reads only the first 3328 (1792) bytes.
+// ---------------------------------------------------------------------------
+template <bool F32>
+struct Rec;
+
+template <>
+struct Rec<false> {
+  static constexpr int SLOT_BYTES = 512;
+  static constexpr int BYTES = 13824;
+  static constexpr int ASTRO = 0, GLOB = 2560, STAR = 3072, INSTR_V = 3328, INSTR_I = 6400,
+                       ATT_V = 7168, ATT_S = 13312, POS = 13568;
+};
+template <>
+struct Rec<true> {
+  static constexpr int SLOT_BYTES = 256;
+  static constexpr int BYTES = 7680;
+  static constexpr int ASTRO = 0, GLOB = 1280, STAR = 1536, INSTR_V = 1792, INSTR_I = 3328,
+                       ATT_V = 4096, ATT_S = 7168, POS = 7424;
+};
+
+// Byte offset of slot t's chunk inside a record.
+template <bool F32>
+__host__ __device__ constexpr int slot_offset(int t) {
+  using R = Rec<F32>;
+  return t < 5 ? R::ASTRO + t * R::SLOT_BYTES
+         : t < 17 ? R::ATT_V + (t - 5) * R::SLOT_BYTES
+         : t < 23 ? R::INSTR_V + (t - 17) * R::SLOT_BYTES
+                  : R::GLOB;
+}
 
 // ---------------------------------------------------------------------------
 // Float-pair ("float-float") arithmetic. A value is hi + lo with |lo| <= ulp(hi)/2.
@@ -39,16 +93,22 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return ff{s, __fadd_rn(__fadd_rn(a.l, b.l), e)};
 }
 
-// Product of two pairs to ~2^-47 relative (the lo*lo term is dropped).
+// Renormalise a pair (exactly): after cancellation in ff_add the low part can
+// be as large as the high part, and products below assume it is not.
+__device__ __forceinline__ ff ff_norm(ff a) {
+  float s, e;
+  two_sum(a.h, a.l, s, e);
+  return ff{s, e};
+}
+
+// Product of two pairs to ~2^-47 relative (the lo*lo term is dropped; the
+// operands must be normalised pairs).
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   float p = __fmul_rn(a.h, b.h);
   float e = __fmaf_rn(a.h, b.h, -p);
   float c = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
   return ff{p, c};
 }
-
-// acc += a * b
-__device__ __forceinline__ void ff_fma_acc(ff& acc, ff a, ff b) { acc = ff_add(acc, ff_mul(a, b)); }
 
 // Product of an FP32 value with a pair.
 __device__ __forceinline__ ff f_mul(float a, ff b) {
@@ -86,40 +146,89 @@ __device__ __forceinline__ double warp_sum_d(double a) {
 }
 
 // ---------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk) completing on an mbarrier, with bounded
+// waits. A wait that runs out sets the error word and returns false.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+// Make mbarrier initialisation and earlier generic shared-memory accesses
+// visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr int WAIT_LIMIT = 1 << 22;  // try_wait rounds before giving up (seconds)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (int i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, GSR_E_TIMEOUT);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // Device layout of one system (all pointers are device memory owned by it).
-// Rows are grouped in warp tiles of TILE_ROWS; lane l of a tile owns rows
-// tile*128 + 4l + j (j = 0..3). Row order is the caller's (star-sorted) order.
 // ---------------------------------------------------------------------------
 struct Layout {
   int64_t n_rows, n_stars, n_knots, n_instr, n_unk;
   int32_t n_glob;
-  int64_t n_tiles;
+  int64_t n_recs;                       // 64-row records (last one padded)
   int64_t att_base, instr_base, glob_col;
-  // Values as float pairs: float4 at [((tile*24 + slot)*2 + q)*32 + lane] holds
-  // rows 4l+2q, 4l+2q+1 as (hi0, lo0, hi1, lo1). 192 B per row.
-  const float4* vals_ff;
-  // FP32-rounded values (mixed precision): float2 at [((tile*24+slot)*2+q)*32+lane]
-  // holds rows 4l+2q, 4l+2q+1. 96 B per row. Null unless F32_PLUS_F64.
-  const float2* vals_f32;
-  const int4* star;       // [tile*32 + lane] star index of rows 4l..4l+3
-  const int4* att_s;      // [tile*32 + lane] start knot s_i of rows 4l..4l+3
-  const int4* att_pos;    // [tile*32 + lane] position of the row in knot order
-  const ushort4* instr;   // [(tile*6 + k)*32 + lane] instrumental index k of rows 4l..4l+3
-  // Attitude coefficients in knot order (rows sorted by s, stable):
-  const float2* att_knot_ff;   // [t][n_rows], t = 4*axis + j
-  const float* att_knot_f32;   // [t][n_rows] FP32-rounded copy (or null)
-  const int64_t* knot_start;   // [n_knots + 1] first position of start knot s
-  const int32_t* att_warp_knot; // [n_att_warps + 1] start-knot range of each attitude warp
+  const unsigned char* rec_ff;          // n_recs x Rec<false>::BYTES
+  const unsigned char* rec_f32;         // n_recs x Rec<true>::BYTES, or null
+  const int32_t* pos;                   // [n_rows] knot-order position of each row
+  // attitude coefficients in knot order (rows stably sorted by start knot s)
+  const float2* att_knot_ff;            // [t][n_rows], t = 4*axis + j
+  const float* att_knot_f32;            // [t][n_rows] FP32 copy (or null)
+  const int64_t* knot_start;            // [n_knots - 3 + 1] first position of start knot s
+  const int32_t* att_warp_knot;         // [n_att_warps + 1] start-knot range of each warp
   int32_t n_att_warps;
-  const int64_t* row_tile_warp; // [n_main_warps + 1] tile range of each star-order warp
-  int32_t n_main_warps;
+  // instrumental entries of each tile of ct_rows rows, in rounds of distinct bins
+  int64_t n_ctiles;
+  int32_t ct_rows;                      // power of two in [64, 2048]
+  const int32_t* ct_round;              // [n_ctiles + 1] first round of each tile
+  const int64_t* round_entry;           // [n_rounds + 1] first entry of each round
+  const float2* ient_ff;                // [6 n_rows] coefficient (pair)
+  const float* ient_f32;                // [6 n_rows] coefficient (FP32 copy) or null
+  const uint32_t* ient_key;             // [6 n_rows] (row in tile << 15) | bin
+  int* err;                             // device error word (GSR_E_TIMEOUT)
 };
 
 struct Scratch {
   double* red;          // partial-sum slots for last-block reductions
   unsigned int* count;  // arrival counters (one per reduction site)
   float2* x_ff;         // [n_unk] float-pair copy of an aprod 1 input
-  double* y_knot;       // [n_rows] aprod 2 input in knot order
+  float2* x3;           // [(n_knots-3) * 12] attitude part of an aprod 1 input,
+                        // x[axis*K + s + j] at [s*12 + axis*4 + j] (96 B per start knot)
+  float2* y_ff;         // [n_pad] float-pair copy of an aprod 2 input (zero padding)
+  float2* y_knot;       // [n_rows] the same in knot order
 };
 
 }  // namespace gsr
@@ -131,21 +240,23 @@ struct gsr_system {
   gsr::Layout L;
   gsr::Scratch S;
   // owned allocations
-  float4* vals_ff;
-  float2* vals_f32;
-  int4* star;
-  int4* att_s;
-  int4* att_pos;
-  ushort4* instr;
+  unsigned char* rec_ff;
+  unsigned char* rec_f32;
+  int32_t* pos;
   float2* att_knot_ff;
   float* att_knot_f32;
   int64_t* knot_start;
   int32_t* att_warp_knot;
-  int64_t* row_tile_warp;
+  int32_t* ct_round;
+  int64_t* round_entry;
+  float2* ient_ff;
+  float* ient_f32;
+  uint32_t* ient_key;
+  int* err;
   double* colnorm;       // [n_unk] ||A_:,j|| (FP64 values)
   // LSQR work vectors (allocated on first solve)
-  double* u;             // [n_rows] unnormalised u
-  double* u_knot;        // [n_rows] u in knot order
+  float2* u;             // [n_pad] unnormalised u as float pairs (zero padding)
+  float2* u_knot;        // [n_rows] u in knot order
   double* v;             // [n_unk]
   double* w;             // [n_unk]
   double* xz;            // [n_unk] iterate of the scaled problem
@@ -156,21 +267,44 @@ struct gsr_system {
   double* host_scal;     // pinned mirror of scal
   cudaStream_t side;     // second stream for the attitude part of aprod 2
   cudaEvent_t ev_fork, ev_join;
-  int main_block, main_ctas, hist_bytes;
+  int main_block, main_ctas, main_smem;
+  int a1_ctas;
 };
 
 // Internal entry points shared between translation units.
 namespace gsr {
-// y = coef*y + A x (coef = *coef_dev if non-null); optional knot-order copy,
-// ||y||^2 into *norm_slot; the kernel does nothing when *stop != 0.
+// Rows padded up to a whole number of instrumental tiles (float-pair vectors
+// over the rows are allocated with this length, the padding zeroed).
+inline int64_t padded_rows(const Layout& L) {
+  const int64_t ct = L.ct_rows > 0 ? L.ct_rows : REC_ROWS;
+  return ((L.n_rows + ct - 1) / ct) * ct + REC_ROWS;
+}
+// y = coef*y + A x on a double y (coef = *coef_dev if non-null), ||y||^2 into
+// *norm_slot; y_knot must be null. The kernel does nothing when *stop != 0.
+// The attitude unknowns are gathered from x_ff directly (no scratch).
 int launch_aprod1(gsr_system* sys, int which_values, const float2* x_ff, double* y,
                   const double* coef_dev, double coef_host, double* y_knot, double* norm_slot,
                   const double* stop, cudaStream_t st);
-// x += A^T y (y_knot = y in knot order); nothing when *stop != 0.
-int launch_aprod2(gsr_system* sys, int which_values, const double* y, const double* y_knot,
+// y += A x on a double y, the attitude unknowns read from sys->S.x3 (built by
+// launch_att_x3 from the same x_ff).
+int launch_aprod1_x3(gsr_system* sys, int which_values, const float2* x_ff, double* y,
+                     cudaStream_t st);
+// y = coef*y + A x on a float-pair y (LSQR's u), attitude from sys->S.x3, with
+// the optional knot-order copy.
+int launch_aprod1_ff(gsr_system* sys, int which_values, const float2* x_ff, float2* y,
+                     const double* coef_dev, float2* y_knot, double* norm_slot,
+                     const double* stop, cudaStream_t st);
+// x += A^T y, y and y_knot (y in knot order) as float pairs, y zero-padded to
+// padded_rows(); nothing when *stop != 0.
+int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const float2* y_knot,
                   double* x, const double* stop, cudaStream_t st);
 int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, cudaStream_t st);
-int launch_scatter_knot(gsr_system* sys, const double* y, double* y_knot, cudaStream_t st);
+// Interleave the attitude part of a float-pair aprod 1 input by start knot
+// (into sys->S.x3); aprod 1 reads it with three 32-byte loads per row.
+int launch_att_x3(gsr_system* sys, const float2* x_ff, const double* stop, cudaStream_t st);
+// y (double) -> y_ff (row order) and y_knot (knot order) as float pairs.
+int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
+                      cudaStream_t st);
 int cuda_status(cudaError_t e);
-int set_kernel_attributes(int hist_bytes);
+int set_kernel_attributes();
 }  // namespace gsr

@@ -91,16 +91,17 @@ __device__ bool grid_sum3(double& a, double& b, double& c, double* part, unsigne
 // ---------------------------------------------------------------------------
 // Start: u~ = b (and its knot-order copy), ||b||^2.
 // ---------------------------------------------------------------------------
-__global__ void k_init_u(Layout L, const double* __restrict__ b, double* __restrict__ u,
-                         double* __restrict__ u_knot, double* scal, double* part,
+__global__ void k_init_u(Layout L, const double* __restrict__ b, float2* __restrict__ u,
+                         float2* __restrict__ u_knot, double* scal, double* part,
                          unsigned int* counter) {
-  const int32_t* pos = reinterpret_cast<const int32_t*>(L.att_pos);
+  const int32_t* pos = L.pos;
   double s2 = 0.0, z0 = 0.0, z1 = 0.0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
        r += (int64_t)gridDim.x * blockDim.x) {
     const double v = b[r];
-    u[r] = v;
-    u_knot[pos[r]] = v;
+    const ff f = ff_from_double(v);
+    u[r] = make_float2(f.h, f.l);
+    u_knot[pos[r]] = make_float2(f.h, f.l);
     s2 = __fma_rn(v, v, s2);
   }
   if (grid_sum3(s2, z0, z1, part, counter) && threadIdx.x == 0) scal[S_UNORM2] = s2;
@@ -296,7 +297,7 @@ int ensure_work(gsr_system* s) {
   auto A = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 8);
   };
-  A((void**)&s->u, n * 8);
+  A((void**)&s->u, padded_rows(s->L) * 8);
   A((void**)&s->u_knot, n * 8);
   A((void**)&s->v, m * 8);
   A((void**)&s->w, m * 8);
@@ -306,6 +307,7 @@ int ensure_work(gsr_system* s) {
   A((void**)&s->v_ff, m * 8);
   A((void**)&s->scal, S_COUNT * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_scal, S_COUNT * 8);
+  if (e == cudaSuccess) e = cudaMemset(s->u, 0, padded_rows(s->L) * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
@@ -323,7 +325,7 @@ struct Ctx {
   double* rn_dev;
 };
 
-constexpr int LAUNCHES_PER_ITERATION = 6;  // aprod1, zero, aprod2 (2), vec_a, vec_b
+constexpr int LAUNCHES_PER_ITERATION = 8;  // x3, aprod1, zero, aprod2 (3), vec_a, vec_b
 
 // Events (4 per iteration) bracket aprod 1, aprod 2 and the vector kernels.
 int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
@@ -332,8 +334,10 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   double* scal = s->scal;
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_unk + 255) / 256 + 1);
   if (ev) cudaEventRecordWithFlags(ev[0], c.st, cudaEventRecordExternal);
-  int rc = launch_aprod1(s, c.which_values, s->v_ff, s->u, scal + S_COEF_U, 0.0, s->u_knot,
-                         scal + S_UNORM2, scal + S_DONE, c.st);
+  int rc = launch_att_x3(s, s->v_ff, scal + S_DONE, c.st);
+  if (rc != GSR_OK) return rc;
+  rc = launch_aprod1_ff(s, c.which_values, s->v_ff, s->u, scal + S_COEF_U, s->u_knot,
+                            scal + S_UNORM2, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
   k_zero<<<vb, 256, 0, c.st>>>(L.n_unk, s->z, scal);
   if (ev) cudaEventRecordWithFlags(ev[1], c.st, cudaEventRecordExternal);
@@ -533,7 +537,7 @@ int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_o
   if (opts->precond < GSR_PRECOND_NONE || opts->precond > GSR_PRECOND_USER) return GSR_E_ARG;
   if (opts->precond == GSR_PRECOND_USER && !opts->scale) return GSR_E_ARG;
   if (opts->precision != GSR_PREC_F64 && opts->precision != GSR_PREC_MIXED) return GSR_E_ARG;
-  if (opts->precision == GSR_PREC_MIXED && !sys->vals_f32) return GSR_E_ARG;
+  if (opts->precision == GSR_PREC_MIXED && !sys->rec_f32) return GSR_E_ARG;
   if (opts->atol < 0 || opts->btol < 0 || opts->conlim < 0 || opts->itnlim < 0) return GSR_E_ARG;
   if ((opts->err_hist && !opts->x_ref)) return GSR_E_ARG;
   std::memset(res, 0, sizeof(*res));
