@@ -204,6 +204,47 @@ def run_reference(args):
     return 0
 
 
+def timed_solves(S, b, x, steps, stream, **solve):
+    """Run `steps` solves back to back; per-step device time (CUDA events on the
+    solve stream) and the per-solve results."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    res = []
+    ev[0].record(stream)
+    for k in range(steps):
+        res.append(S.lsqr(b, x=x, **solve))
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)], res
+
+
+def bench_mixed(S, b, x_ref, args, stream, dev):
+    """Mixed precision (FP32-stored A + FP64 correction): find the phase-1 length
+    and the phase-2 iterations to 1e-9, then time solves of exactly that shape."""
+    import torch
+    probe = S.lsqr(b, atol=1e-15, btol=1e-15, precision="mixed", itnlim=5000, x_ref=x_ref,
+                   err_hist=True)
+    eh = probe["err_hist"]
+    n1 = probe["itn"] - probe["phase2_itn"]
+    ok = np.nonzero(eh[n1:] <= TARGET_ERR)[0]
+    n2 = int(ok[0]) + 1 if ok.size else int(probe["phase2_itn"])
+    x = torch.empty(S.n_unk, dtype=torch.float64, device=dev)
+    solve = dict(atol=0.0, btol=0.0, conlim=0.0, precision="mixed", mixed_switch_itn=n1,
+                 itnlim=n1 + n2)
+    for _ in range(args.warmup):
+        S.lsqr(b, x=x, **solve)
+    ms, res = timed_solves(S, b, x, args.steps, stream, profile=True, **solve)
+    err = float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))
+    nt = sum(r["n_timed_itn"] for r in res)
+    log("mixed: phase 1 %d + phase 2 %d iterations, %.1f ms, err %.2e" % (n1, n2, np.mean(ms), err))
+    return {"value": float(np.mean(ms)) / 1e3, "unit": "s", "phase1_itn_fp32": n1,
+            "phase2_itn_fp64": n2, "fp32_phase_rel_err": float(eh[n1 - 1]),
+            "final_rel_err": err,
+            "aprod1_ms_mean": sum(r["t_aprod1_ms"] for r in res) / max(nt, 1),
+            "aprod2_ms_mean": sum(r["t_aprod2_ms"] for r in res) / max(nt, 1),
+            "gpu_launches": int(sum(r["n_launches"] for r in res))}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -218,7 +259,7 @@ def run_ours(args):
 
     sys_ = make_workload(args.workload)
     t0 = time.perf_counter()
-    S = gsr.System(sys_, device=local)
+    S = gsr.System(sys_, device=local, storage="f32+f64" if args.variants else "f64")
     log("gsr_create: %.1f s" % (time.perf_counter() - t0))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
@@ -282,6 +323,10 @@ def run_ours(args):
             e2e.append(time.perf_counter() - t0)
         barrier()
 
+        variants = {}
+        if args.variants:
+            variants["mixed"] = bench_mixed(S, b, x_ref, args, stream, dev)
+
     ms = float(np.mean(step_ms))
     if dist is not None:
         t = torch.tensor([ms, float(np.median(e2e))], dtype=torch.float64, device=dev)
@@ -323,6 +368,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if variants:
+        line["variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         bh = b.detach().cpu().numpy()
@@ -349,6 +396,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="medium", choices=["tiny", "small", "medium", "large"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the mixed-precision / batched variants")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -678,6 +678,21 @@ int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, c
   return cuda_status(cudaGetLastError());
 }
 
+__global__ void k_to_ff_neg(const double* __restrict__ x, float2* __restrict__ out, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const ff f = ff_from_double(-x[j]);
+    out[j] = make_float2(f.h, f.l);
+  }
+}
+
+int launch_to_ff_neg(const double* x, float2* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return GSR_OK;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  k_to_ff_neg<<<blocks, 256, 0, st>>>(x, out, n);
+  return cuda_status(cudaGetLastError());
+}
+
 int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
                       cudaStream_t st) {
   if (sys->L.n_rows <= 0) return GSR_OK;

@@ -115,7 +115,8 @@ void free_system(gsr_system* s) {
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
                   s->att_warp_knot, s->ct_round, s->round_entry, s->ient_ff, s->ient_f32,
                   s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
-                  s->dscale, s->v_ff, s->scal, s->S.red, s->S.count, s->S.x_ff, s->S.x3,
+                  s->dscale, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
+                  s->S.count, s->S.x_ff, s->S.x3,
                   s->S.y_ff, s->S.y_knot};
   for (void* p : ptrs)
     if (p) cudaFree(p);

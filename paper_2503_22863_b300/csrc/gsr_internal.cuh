@@ -263,6 +263,9 @@ struct gsr_system {
   double* z;             // [n_unk] A^T u accumulator
   double* dscale;        // [n_unk] column scaling in use
   float2* v_ff;          // [n_unk] float-pair D v (aprod 1 input)
+  double* mx_x1;         // mixed precision: phase-1 solution [n_unk]
+  double* mx_d;          // mixed precision: correction [n_unk]
+  double* mx_r;          // mixed precision: residual b - A x1 [n_rows]
   double* scal;          // device LSQR scalars
   double* host_scal;     // pinned mirror of scal
   cudaStream_t side;     // second stream for the attitude part of aprod 2
@@ -299,6 +302,8 @@ int launch_aprod1_ff(gsr_system* sys, int which_values, const float2* x_ff, floa
 int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const float2* y_knot,
                   double* x, const double* stop, cudaStream_t st);
 int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, cudaStream_t st);
+// out = -x as float pairs.
+int launch_to_ff_neg(const double* x, float2* out, int64_t n, cudaStream_t st);
 // Interleave the attitude part of a float-pair aprod 1 input by start knot
 // (into sys->S.x3); aprod 1 reads it with three 32-byte loads per row.
 int launch_att_x3(gsr_system* sys, const float2* x_ff, const double* stop, cudaStream_t st);

@@ -169,8 +169,9 @@ __global__ void k_vec_a(int64_t n, const double* __restrict__ d, const double* _
 __global__ void k_vec_b(int64_t n, const double* __restrict__ d, double* __restrict__ v,
                         double* __restrict__ w, double* __restrict__ xz,
                         float2* __restrict__ v_ff, double* __restrict__ var,
-                        const double* __restrict__ x_ref, double* scal, double* part,
-                        unsigned int* counter, int first, double* err_hist, double* rnorm_hist) {
+                        const double* __restrict__ x_ref, const double* __restrict__ x_off,
+                        double* scal, double* part, unsigned int* counter, int first,
+                        double* err_hist, double* rnorm_hist) {
   if (scal[S_DONE] != 0.0) return;
   const double alpha = scal[S_ALPHA];
   const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
@@ -202,7 +203,7 @@ __global__ void k_vec_b(int64_t n, const double* __restrict__ d, double* __restr
     const ff f = ff_from_double(dj * vn);
     v_ff[j] = make_float2(f.h, f.l);
     if (x_ref) {
-      const double e = xv - x_ref[j];
+      const double e = (x_off ? xv + x_off[j] : xv) - x_ref[j];
       e2 = __fma_rn(e, e, e2);
     }
   }
@@ -321,6 +322,7 @@ struct Ctx {
   int which_values;
   double* var;
   const double* x_ref;
+  const double* x_off;
   double* err_dev;
   double* rn_dev;
 };
@@ -346,17 +348,19 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   if (ev) cudaEventRecordWithFlags(ev[2], c.st, cudaEventRecordExternal);
   k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 0);
   k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
-                                scal, s->S.red, s->S.count + 2, 0, c.err_dev, c.rn_dev);
+                                c.x_off, scal, s->S.red, s->S.count + 2, 0, c.err_dev, c.rn_dev);
   if (ev) cudaEventRecordWithFlags(ev[3], c.st, cudaEventRecordExternal);
   return cuda_status(cudaGetLastError());
 }
 
 }  // namespace
 
+// One LSQR solve of min ||A x - b|| on the chosen copy of the values. x_off
+// (optional) is added to the iterate when measuring the error against x_ref
+// (the correction phase of the mixed-precision solve).
 int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
-             gsr_lsqr_result* res, cudaStream_t st, int which_values, bool keep_state,
+             gsr_lsqr_result* res, cudaStream_t st, int which_values, const double* x_off,
              int64_t itnlim) {
-  (void)keep_state;
   const Layout& L = s->L;
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_unk + 255) / 256 + 1);
   const int rb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_rows + 255) / 256 + 1);
@@ -391,13 +395,14 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (rc != GSR_OK) return rc;
   k_vec_a<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 1);
   k_vec_b<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, o->var,
-                              o->x_ref && err_dev ? o->x_ref : nullptr, scal, s->S.red,
+                              o->x_ref && err_dev ? o->x_ref : nullptr, x_off, scal, s->S.red,
                               s->S.count + 2, 1, nullptr, nullptr);
   C(cudaGetLastError());
   if (e != cudaSuccess) return GSR_E_CUDA;
 
   int64_t n_launches = 7 + (o->var ? 1 : 0) + ((o->x_ref && err_dev) ? 1 : 0);
-  Ctx c{s, st, which_values, o->var, (o->x_ref && err_dev) ? o->x_ref : nullptr, err_dev, rn_dev};
+  Ctx c{s, st, which_values, o->var, (o->x_ref && err_dev) ? o->x_ref : nullptr, x_off, err_dev,
+        rn_dev};
   // Capture a chunk of iterations once and replay it.
   const int chunk = 4;
   const bool prof = o->profile != 0;
@@ -509,6 +514,79 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   return GSR_OK;
 }
 
+__global__ void k_axpy_into(int64_t n, double a, const double* __restrict__ xa,
+                            const double* __restrict__ xb, double* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = __fma_rn(a, xa[j], xb[j]);
+}
+
+// Mixed precision (FP32-stored A, FP64 correction):
+//   phase 1: LSQR with the FP32-rounded values (half the matrix bytes; float-pair
+//            arithmetic and FP64 vectors/scalars as everywhere) to about FP32 accuracy;
+//   phase 2: r = b - A x1 with the full-precision values, then LSQR on
+//            min ||A d - r|| with the full-precision values and the caller's
+//            tolerances; x = x1 + d. Phase 2 uses the full-precision matrix in
+//            both products, so its fixed point is the full-precision solution.
+int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
+               gsr_lsqr_result* res, cudaStream_t st, int64_t itnlim) {
+  const int64_t n = s->L.n_rows, m = s->L.n_unk;
+  if (!s->mx_x1) {
+    cudaError_t e = cudaMalloc((void**)&s->mx_x1, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->mx_d, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->mx_r, (n > 0 ? n : 1) * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
+    }
+  }
+  constexpr double PHASE1_TOL = 1e-7;  // about the relative size of FP32 rounding of A
+  gsr_lsqr_opts o1 = *o;
+  int64_t lim1 = itnlim;
+  if (o->mixed_switch_itn > 0) {
+    o1.atol = o1.btol = 0.0;
+    o1.conlim = 0.0;
+    lim1 = std::min<int64_t>(itnlim, o->mixed_switch_itn);
+  } else {
+    o1.atol = std::max(o->atol, PHASE1_TOL);
+    o1.btol = std::max(o->btol, PHASE1_TOL);
+  }
+  o1.rnorm_hist = nullptr;
+  gsr_lsqr_result r1;
+  std::memset(&r1, 0, sizeof(r1));
+  int rc = lsqr_run(s, b, s->mx_x1, &o1, &r1, st, GSR_VALUES_F32, nullptr, lim1);
+  if (rc != GSR_OK) return rc;
+  // r = b - A x1 with the full-precision values
+  const int vb = (int)std::min<int64_t>(RED_BLOCKS, (m + 255) / 256 + 1);
+  cudaError_t e = cudaMemcpyAsync(s->mx_r, b, n * 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  rc = launch_to_ff_neg(s->mx_x1, s->S.x_ff, m, st);
+  if (rc != GSR_OK) return rc;
+  rc = launch_att_x3(s, s->S.x_ff, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  rc = launch_aprod1_x3(s, GSR_VALUES_F64, s->S.x_ff, s->mx_r, st);
+  if (rc != GSR_OK) return rc;
+  // phase 2
+  gsr_lsqr_opts o2 = *o;
+  o2.var = nullptr;
+  const int64_t n1 = r1.itn;
+  o2.err_hist = o->err_hist ? o->err_hist + n1 : nullptr;
+  o2.rnorm_hist = o->rnorm_hist ? o->rnorm_hist + n1 : nullptr;
+  const int64_t lim2 = std::max<int64_t>(1, itnlim - n1);
+  rc = lsqr_run(s, s->mx_r, s->mx_d, &o2, res, st, GSR_VALUES_F64, s->mx_x1, lim2);
+  if (rc != GSR_OK) return rc;
+  k_axpy_into<<<vb, 256, 0, st>>>(m, 1.0, s->mx_d, s->mx_x1, x);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GSR_E_CUDA;
+  res->phase2_itn = (int32_t)res->itn;
+  res->itn += n1;
+  res->n_launches += r1.n_launches + 5;
+  res->n_timed_itn += r1.n_timed_itn;
+  res->t_aprod1_ms += r1.t_aprod1_ms;
+  res->t_aprod2_ms += r1.t_aprod2_ms;
+  res->t_vector_ms += r1.t_vector_ms;
+  return GSR_OK;
+}
+
 int setup_scaling(gsr_system* s, const gsr_lsqr_opts* o, cudaStream_t st) {
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (s->L.n_unk + 255) / 256 + 1);
   k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->dscale);
@@ -553,7 +631,8 @@ int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_o
     res->istop = 0;
     return gsr::cuda_status(cudaStreamSynchronize(st));
   }
-  return gsr::lsqr_run(sys, b, x, opts, res, st, GSR_VALUES_F64, false, itnlim);
+  if (opts->precision == GSR_PREC_MIXED) return gsr::lsqr_mixed(sys, b, x, opts, res, st, itnlim);
+  return gsr::lsqr_run(sys, b, x, opts, res, st, GSR_VALUES_F64, nullptr, itnlim);
 }
 
 }  // extern "C"
