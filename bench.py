@@ -245,6 +245,45 @@ def bench_mixed(S, b, x_ref, args, stream, dev):
             "gpu_launches": int(sum(r["n_launches"] for r in res))}
 
 
+def bench_batched(S, sys_, k, ms_single, args, stream, dev):
+    """k right-hand sides b_j = A x* + noise_j (noise drawn on the device from a
+    fixed seed) solved at once: time until every one reaches 1e-9."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(2504 * 100 + k)
+    xs = torch.from_numpy(sys_["x_star"]).to(dev)
+    Xs = xs[:, None].repeat(1, k).contiguous()
+    B = torch.randn((S.n_rows, k), generator=g, dtype=torch.float64, device=dev) * 1e-3
+    S.aprod1_batch(Xs, B)
+    ref = S.lsqr_batch(B, atol=1e-15, btol=1e-15, itnlim=5000)
+    x_ref = ref["x"].clone()
+    probe = S.lsqr_batch(B, atol=0.0, btol=0.0, conlim=0.0, itnlim=max(ref["itn"]) + 20,
+                         x_ref=x_ref, err_hist=True)
+    worst = probe["err_hist"].max(axis=1)
+    ok = np.nonzero(worst <= TARGET_ERR)[0]
+    n_star = int(ok[0]) + 1 if ok.size else int(max(ref["itn"]))
+    X = torch.empty((S.n_unk, k), dtype=torch.float64, device=dev)
+    solve = dict(atol=0.0, btol=0.0, conlim=0.0, itnlim=n_star)
+    S.lsqr_batch(B, X=X, **solve)
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    res = None
+    for i in range(steps):
+        res = S.lsqr_batch(B, X=X, **solve)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = float(np.mean([ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]))
+    err = float((torch.linalg.norm(X - x_ref, dim=0) / torch.linalg.norm(x_ref, dim=0)).max())
+    log("batched k=%d: %d iterations, %.1f ms (%.1f ms per right-hand side), worst err %.2e"
+        % (k, n_star, ms, ms / k, err))
+    return {"value": ms / 1e3, "unit": "s", "k": k, "iterations_to_1e9": n_star,
+            "s_per_rhs": ms / 1e3 / k, "speedup_vs_k_single_solves": k * ms_single / ms,
+            "worst_final_rel_err": err, "tuning": S.batch_tuning(),
+            "gpu_launches": int(res["n_launches"]) * steps}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,6 +365,9 @@ def run_ours(args):
         variants = {}
         if args.variants:
             variants["mixed"] = bench_mixed(S, b, x_ref, args, stream, dev)
+            for kk in args.batch_k:
+                variants["batched_k%d" % kk] = bench_batched(S, sys_, kk, ms_single=float(
+                    np.mean(step_ms)), args=args, stream=stream, dev=dev)
 
     ms = float(np.mean(step_ms))
     if dist is not None:
@@ -398,6 +440,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision / batched variants")
+    ap.add_argument("--batch-k", type=int, nargs="*", default=[8, 32],
+                    help="right-hand-side counts of the batched variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

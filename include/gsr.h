@@ -169,6 +169,32 @@ void gsr_lsqr_default_opts(gsr_lsqr_opts* opts);
 int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_opts* opts,
                    gsr_lsqr_result* res, void* stream);
 
+/*
+ * Multi-right-hand-side forms: k systems sharing A (1 <= k <= 32), e.g.
+ * Monte-Carlo perturbed observation vectors b_j = A x* + noise_j used to
+ * estimate covariances (the quantity of Sec. 2.2, Eq. 4). Vectors are
+ * row-major with the right-hand sides interleaved: Y [n_rows][k], X [N_unk][k],
+ * device. A is read once per product for all k columns.
+ */
+/* Eq. 2 for k columns: Y += A X. */
+int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* stream);
+/* Eq. 3 for k columns: X += A^T Y. */
+int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* stream);
+/*
+ * LSQR on the k systems at once (same A, tolerances and preconditioner;
+ * per-right-hand-side scalars, stopping tests and convergence masks: a system
+ * that has stopped keeps its x while the others continue). res has k entries.
+ * opts.err_hist (host, [itnlim][k]) with opts.x_ref (device [N_unk][k]) gives
+ * per-iteration relative errors. precision must be F64; var and rnorm_hist are
+ * not available here (GSR_E_UNSUPPORTED). The first call for a given k times
+ * the candidate block widths and instrumental chunk sizes on this system and
+ * keeps the fastest (gsr_batch_tuning reports the choice). Synchronous.
+ */
+int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
+                         const gsr_lsqr_opts* opts, gsr_lsqr_result* res, void* stream);
+/* Block width and right-hand sides per instrumental block chosen by the tuner. */
+int gsr_batch_tuning(const gsr_system* sys, int* threads, int* kc);
+
 #ifdef __cplusplus
 }
 #endif

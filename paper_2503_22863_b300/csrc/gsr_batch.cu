@@ -1,0 +1,1096 @@
+// Multi-right-hand-side aprod 1 / aprod 2 and LSQR (k systems A x_j = b_j
+// sharing A, e.g. Monte-Carlo perturbed observation vectors for covariances).
+//
+// aprod becomes a sparse-times-dense-block product that reads A once for all
+// k vectors. Vectors are stored with the right-hand sides interleaved,
+// Y[row][KP] and X[col][KP] (KP = k rounded up to a power of two <= 32), so
+// that lanes run over right-hand sides: a warp is split into 32/KP "streams"
+// of KP lanes; every stream walks rows (or knot-ordered positions, or
+// instrumental entries) while each of its lanes handles one right-hand side.
+// Coefficients are broadcast within a stream and every x / y access is a
+// contiguous KP-wide vector. All arithmetic is float pairs as in the
+// single-right-hand-side kernels. The instrumental histogram (n_instr x KP
+// pairs) does not fit one block's shared memory, so blocks split the
+// right-hand sides into chunks of KC (a tuning parameter).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+namespace {
+
+__device__ __forceinline__ double f2d_bits_b(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)s, 0);
+  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
+  return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+__device__ __forceinline__ void red_ff_b(double* x, ff a) {
+  if (a.h != 0.0f) atomicAdd(x, f2d_bits_b(a.h));
+  if (a.l != 0.0f) atomicAdd(x, f2d_bits_b(a.l));
+}
+
+// Record accessors for row r_in (0..63) of a record (L1/L2-cached loads; the
+// KP lanes of a stream read the same address).
+__device__ __forceinline__ ff rv(const unsigned char* rec, int t, int r_in) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(rec + slot_offset<false>(t) +
+                                                         (r_in >> 1) * 16 + (r_in & 1) * 8));
+  return ff{v.x, v.y};
+}
+__device__ __forceinline__ int ri(const unsigned char* rec, int off, int r_in) {
+  return __ldg(reinterpret_cast<const int*>(rec + off) + r_in);
+}
+__device__ __forceinline__ int rinstr(const unsigned char* rec, int k, int r_in) {
+  return __ldg(reinterpret_cast<const unsigned short*>(rec + Rec<false>::INSTR_I + k * 128) +
+               r_in);
+}
+__device__ __forceinline__ ff ldf(const float2* p) {
+  const float2 a = __ldg(p);
+  return ff{a.x, a.y};
+}
+
+// Per-right-hand-side deterministic grid reduction of NV values per lane:
+// lanes of a block with the same j = threadIdx.x % KP are summed, blocks store
+// part[(block*NV + v)*KP + j], and the last block adds them in block order
+// into tot[v*32 + j] (shared, visible to the whole last block on return true).
+// Blocks of at most 256 threads.
+template <int KP, int NV>
+__device__ bool grid_sum_kv(const double* v, double* part, unsigned int* counter, double* tot) {
+  __shared__ double sh[NV][8][32];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    double x = v[a];
+#pragma unroll
+    for (int m = 16; m >= KP; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+    if (lane < KP) sh[a][wid][lane] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < KP) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double x = 0.0;
+      for (int w = 0; w < nw; ++w) x += sh[a][w][threadIdx.x];
+      part[((size_t)blockIdx.x * NV + a) * KP + threadIdx.x] = x;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  if (threadIdx.x < KP) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double x = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b)
+        x += __ldcg(part + ((size_t)b * NV + a) * KP + threadIdx.x);
+      tot[a * 32 + threadIdx.x] = x;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// aprod 1, k right-hand sides: Y[r][j] = coef[j] Y[r][j] + (A X_j)[r]; optional
+// knot-order copy and per-right-hand-side ||Y_j||^2 into norm_out[j]. A warp
+// takes a record; its 32/KP streams take contiguous slices of the 64 rows.
+// ---------------------------------------------------------------------------
+template <int KP>
+__global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __restrict__ X,
+                                                  float2* __restrict__ Y,
+                                                  const double* __restrict__ coef,
+                                                  float2* __restrict__ Yk, double* part,
+                                                  unsigned int* counter, double* norm_out,
+                                                  const double* stop) {
+  if (stop && *stop != 0.0) return;
+  __shared__ double tot[32];
+  constexpr int S = 32 / KP, RPS = REC_ROWS / S;
+  const int lane = threadIdx.x & 31, q = lane / KP, j = lane % KP;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const ff cf = coef ? ff_from_double(coef[j]) : ff{1.0f, 0.0f};
+  const bool glob = L.n_glob == 1;
+  const int64_t K = L.n_knots;
+  ff nrm = ff_zero();
+  for (int64_t r = gw; r < L.n_recs; r += nw) {
+    const unsigned char* rec = L.rec_ff + r * Rec<false>::BYTES;
+#pragma unroll 2
+    for (int i = 0; i < RPS; ++i) {
+      const int r_in = q * RPS + i;
+      const int64_t row = r * REC_ROWS + r_in;
+      if (row >= L.n_rows) break;
+      const int st = ri(rec, Rec<false>::STAR, r_in);
+      const int sk = ri(rec, Rec<false>::ATT_S, r_in);
+      ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero(), a4 = ff_zero();
+#pragma unroll
+      for (int t = 0; t < 5; ++t)
+        a0 = ff_add(a0, ff_mul(rv(rec, t, r_in), ldf(X + (5 * (int64_t)st + t) * KP + j)));
+#pragma unroll
+      for (int i4 = 0; i4 < 4; ++i4) {
+        a1 = ff_add(a1, ff_mul(rv(rec, 5 + i4, r_in), ldf(X + (L.att_base + sk + i4) * KP + j)));
+        a2 = ff_add(a2, ff_mul(rv(rec, 9 + i4, r_in),
+                               ldf(X + (L.att_base + K + sk + i4) * KP + j)));
+        a3 = ff_add(a3, ff_mul(rv(rec, 13 + i4, r_in),
+                               ldf(X + (L.att_base + 2 * K + sk + i4) * KP + j)));
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        a4 = ff_add(a4, ff_mul(rv(rec, 17 + k, r_in),
+                               ldf(X + (L.instr_base + rinstr(rec, k, r_in)) * KP + j)));
+      if (glob) a4 = ff_add(a4, ff_mul(rv(rec, 23, r_in), ldf(X + L.glob_col * KP + j)));
+      const ff acc = ff_add(ff_add(ff_add(a0, a1), ff_add(a2, a3)), a4);
+      const float2 yo = Y[row * KP + j];
+      const ff yn = ff_norm(ff_add(ff_mul(cf, ff{yo.x, yo.y}), acc));
+      Y[row * KP + j] = make_float2(yn.h, yn.l);
+      if (Yk) Yk[(int64_t)ri(rec, Rec<false>::POS, r_in) * KP + j] = make_float2(yn.h, yn.l);
+      nrm = ff_add(nrm, ff_mul(yn, yn));
+    }
+  }
+  const double nv = ff_to_double(nrm);
+  if (norm_out && grid_sum_kv<KP, 1>(&nv, part, counter, tot) && threadIdx.x < KP)
+    norm_out[threadIdx.x] = tot[threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, k right-hand sides, astrometric + global part: a stream walks a
+// slice of a record's rows keeping per-star sums; a finished (or slice-ending)
+// run is added into X with L2 reductions (KP-wide, contiguous).
+// ---------------------------------------------------------------------------
+template <int KP>
+__global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* __restrict__ Y,
+                                                        double* __restrict__ X,
+                                                        const double* stop) {
+  if (stop && *stop != 0.0) return;
+  constexpr int S = 32 / KP, RPS = REC_ROWS / S;
+  const int lane = threadIdx.x & 31, q = lane / KP, j = lane % KP;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool glob = L.n_glob == 1;
+  ff g = ff_zero();
+  for (int64_t r = gw; r < L.n_recs; r += nw) {
+    const unsigned char* rec = L.rec_ff + r * Rec<false>::BYTES;
+    int cur = -1;
+    ff a[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) a[t] = ff_zero();
+    for (int i = 0; i < RPS; ++i) {
+      const int r_in = q * RPS + i;
+      const int64_t row = r * REC_ROWS + r_in;
+      if (row >= L.n_rows) break;
+      const int st = ri(rec, Rec<false>::STAR, r_in);
+      if (st != cur) {
+        if (cur >= 0)
+#pragma unroll
+          for (int t = 0; t < 5; ++t) red_ff_b(X + (5 * (int64_t)cur + t) * KP + j, a[t]);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) a[t] = ff_zero();
+        cur = st;
+      }
+      const float2 yy = __ldcs(Y + row * KP + j);
+      const ff u = ff{yy.x, yy.y};
+#pragma unroll
+      for (int t = 0; t < 5; ++t) a[t] = ff_add(a[t], ff_mul(rv(rec, t, r_in), u));
+      if (glob) g = ff_add(g, ff_mul(rv(rec, 23, r_in), u));
+    }
+    if (cur >= 0)
+#pragma unroll
+      for (int t = 0; t < 5; ++t) red_ff_b(X + (5 * (int64_t)cur + t) * KP + j, a[t]);
+  }
+  if (glob) {
+#pragma unroll
+    for (int m = 16; m >= KP; m >>= 1) g = ff_add(g, ff_shfl_xor(g, m));
+    if (q == 0) red_ff_b(X + L.glob_col * KP + j, g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, k right-hand sides, attitude part: a warp walks its start-knot
+// range; within a bucket the streams split the positions, then sums are joined
+// across streams and the 4-knot window per axis advances as in the single form.
+// ---------------------------------------------------------------------------
+template <int KP>
+__global__ void __launch_bounds__(256) k_aprod2_att_b(Layout L, const float2* __restrict__ Yk,
+                                                      double* __restrict__ X, const double* stop) {
+  if (stop && *stop != 0.0) return;
+  constexpr int S = 32 / KP;
+  const int lane = threadIdx.x & 31, q = lane / KP, j = lane % KP;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (gwarp >= L.n_att_warps) return;
+  const int s_begin = L.att_warp_knot[gwarp], s_end = L.att_warp_knot[gwarp + 1];
+  if (s_begin >= s_end) return;
+  const int64_t K = L.n_knots;
+  ff win[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) win[a][i] = ff_zero();
+  for (int s = s_begin; s < s_end; ++s) {
+    const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
+    ff acc[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) acc[t] = ff_zero();
+    constexpr int U = 4;  // positions per stream per step, all loads issued first
+    for (int64_t pb = p0 + q; pb < p1; pb += U * S) {
+      ff u[U];
+      float2 v[12][U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int64_t p = pb + (int64_t)i * S;
+        const bool in = p < p1;
+        const float2 yy = in ? __ldcs(Yk + p * KP + j) : make_float2(0.f, 0.f);
+        u[i] = ff{yy.x, yy.y};
+#pragma unroll
+        for (int t = 0; t < 12; ++t)
+          v[t][i] = in ? __ldg(L.att_knot_ff + (int64_t)t * L.n_rows + p) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int t = 0; t < 12; ++t) {
+        ff sum = ff_mul(ff{v[t][0].x, v[t][0].y}, u[0]);
+#pragma unroll
+        for (int i = 1; i < U; ++i) sum = ff_add(sum, ff_mul(ff{v[t][i].x, v[t][i].y}, u[i]));
+        acc[t] = ff_add(acc[t], sum);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+#pragma unroll
+      for (int m = 16; m >= KP; m >>= 1) acc[t] = ff_add(acc[t], ff_shfl_xor(acc[t], m));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) win[a][i] = ff_add(win[a][i], acc[4 * a + i]);
+    if (q == 0)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) red_ff_b(X + (L.att_base + a * K + s) * KP + j, win[a][0]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      win[a][0] = win[a][1];
+      win[a][1] = win[a][2];
+      win[a][2] = win[a][3];
+      win[a][3] = ff_zero();
+    }
+  }
+  if (q == 0)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        red_ff_b(X + (L.att_base + a * K + s_end + i) * KP + j, win[a][i]);
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, k right-hand sides, instrumental part. Block b handles the
+// right-hand sides [c0, c0+kc) (c0 = (b / n_groups) * kc) for the tiles
+// ct = b % n_groups (mod n_groups). A histogram n_instr x kc of pairs and the
+// tile's Y slice live in shared memory; the rounds of distinct bins keep the
+// read-modify-writes conflict free. Entries are read from global memory; the
+// chunk groups walk the same tiles in the same order, so L2 serves repeats.
+// ---------------------------------------------------------------------------
+template <int KP>
+__global__ void __launch_bounds__(512, 1) k_aprod2_instr_b(Layout L, const float2* __restrict__ Y,
+                                                           double* __restrict__ X, int n_groups,
+                                                           int kc, const double* stop) {
+  if (stop && *stop != 0.0) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int CT = L.ct_rows;
+  float2* hist = reinterpret_cast<float2*>(smem);  // [n_instr][kc]
+  float2* ys = hist + L.n_instr * kc;             // [CT][kc]
+  const int group = blockIdx.x % n_groups;
+  const int c0 = (blockIdx.x / n_groups) * kc;
+  const int lkc = __ffs(kc) - 1;  // kc is a power of two
+  for (int i = threadIdx.x; i < L.n_instr * kc; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
+  for (int64_t ct = group; ct < L.n_ctiles; ct += n_groups) {
+    __syncthreads();
+    const int64_t r0 = ct * CT;
+    for (int i = threadIdx.x; i < CT * kc; i += blockDim.x) {
+      const int row = i >> lkc, jj = i & (kc - 1);
+      ys[i] = r0 + row < L.n_rows ? Y[(r0 + row) * KP + c0 + jj] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int64_t ea = L.round_entry[k], eb = L.round_entry[k + 1];
+      const int n_work = (int)(eb - ea) << lkc;
+      const uint32_t* keys = L.ient_key + ea;
+      const float2* vals = L.ient_ff + ea;
+      constexpr int U = 4;  // work items per thread per step, loads issued first
+      for (int wb = threadIdx.x; wb < n_work; wb += U * (int)blockDim.x) {
+        uint32_t key[U];
+        float2 vv[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+          const int w = wb + i * (int)blockDim.x;
+          const bool in = w < n_work;
+          const int e = in ? (w >> lkc) : 0;
+          key[i] = in ? __ldg(keys + e) : 0xffffffffu;
+          vv[i] = in ? __ldg(vals + e) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+          if (key[i] == 0xffffffffu) continue;
+          const int w = wb + i * (int)blockDim.x;
+          const int jj = w & (kc - 1);
+          const int row = (int)(key[i] >> INSTR_BIN_BITS);
+          const int bin = (int)(key[i] & ((1u << INSTR_BIN_BITS) - 1));
+          const float2 uu = ys[row * kc + jj];
+          const ff p = ff_mul(ff{vv[i].x, vv[i].y}, ff{uu.x, uu.y});
+          const float2 h = hist[bin * kc + jj];
+          const ff nh = ff_add(ff{h.x, h.y}, p);
+          hist[bin * kc + jj] = make_float2(nh.h, nh.l);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < L.n_instr * kc; i += blockDim.x) {
+    const float2 h = hist[i];
+    red_ff_b(X + (L.instr_base + (i >> lkc)) * KP + c0 + (i & (kc - 1)), ff{h.x, h.y});
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Conversions between the caller layout [n][k] (double) and [n][KP] pairs.
+// ---------------------------------------------------------------------------
+__global__ void k_pack_ff(const double* __restrict__ in, int k, int KP, int64_t n,
+                          float2* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / KP;
+    const int j = (int)(e % KP);
+    const ff f = ff_from_double(j < k ? in[i * k + j] : 0.0);
+    out[e] = make_float2(f.h, f.l);
+  }
+}
+__global__ void k_pack_ff_knot(Layout L, const double* __restrict__ in, int k, int KP,
+                               float2* __restrict__ out, float2* __restrict__ outk) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.n_rows * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / KP;
+    const int j = (int)(e % KP);
+    const ff f = ff_from_double(j < k ? in[i * k + j] : 0.0);
+    out[e] = make_float2(f.h, f.l);
+    outk[(int64_t)L.pos[i] * KP + j] = make_float2(f.h, f.l);
+  }
+}
+__global__ void k_unpack_ff(const float2* __restrict__ in, int k, int KP, int64_t n,
+                            double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = in[(e / k) * KP + e % k];
+    out[e] = ff_to_double(ff{v.x, v.y});
+  }
+}
+__global__ void k_add_cols(const double* __restrict__ in, int k, int KP, int64_t n,
+                           double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] += in[(e / k) * KP + e % k];
+}
+__global__ void k_zero_d(double* __restrict__ a, int64_t n, const double* stop) {
+  if (stop && *stop != 0.0) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    a[e] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Batched LSQR. Per-right-hand-side scalars at sc[s*KP + j] (s an enum BS
+// slot), global words after them. A right-hand side whose stopping test fired
+// is frozen: its coefficient and D v are zeroed so its u stays 0, and its x
+// and w stop changing; all kernels return at once when every one stopped.
+// ---------------------------------------------------------------------------
+enum BS {
+  B_ALPHA = 0, B_BETA, B_RHOBAR, B_PHIBAR, B_ANORM2, B_DDNORM, B_BNORM, B_RHO, B_C, B_T1, B_T2,
+  B_RNORM, B_ARNORM, B_ACOND, B_XNORM, B_ITN, B_ISTOP, B_DONE, B_UNORM2, B_COEF, B_XREF2,
+  B_COUNT
+};
+enum BG { G_ALLDONE = 0, G_ATOL, G_BTOL, G_CTOL, G_ITNLIM, G_K, G_ITER, G_COUNT };
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_init_b(Layout L, const double* __restrict__ B, int k,
+                                                float2* __restrict__ U, float2* __restrict__ Uk,
+                                                double* sc, double* part, unsigned int* counter) {
+  __shared__ double tot[32];
+  double s2 = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.n_rows * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / KP;
+    const int j = (int)(e % KP);
+    const double v = j < k ? B[i * k + j] : 0.0;
+    const ff f = ff_from_double(v);
+    U[e] = make_float2(f.h, f.l);
+    Uk[(int64_t)L.pos[i] * KP + j] = make_float2(f.h, f.l);
+    s2 = __fma_rn(v, v, s2);
+  }
+  if (grid_sum_kv<KP, 1>(&s2, part, counter, tot) && threadIdx.x < KP)
+    sc[B_UNORM2 * KP + threadIdx.x] = tot[threadIdx.x];
+}
+
+// ||x_ref_j||^2 for the error history.
+template <int KP>
+__global__ void __launch_bounds__(256) k_xref2_b(int64_t n, const double* __restrict__ xr,
+                                                 double* sc, double* part, unsigned int* counter) {
+  __shared__ double tot[32];
+  double s2 = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+       e += (int64_t)gridDim.x * blockDim.x)
+    s2 = __fma_rn(xr[e], xr[e], s2);
+  if (grid_sum_kv<KP, 1>(&s2, part, counter, tot) && threadIdx.x < KP)
+    sc[B_XREF2 * KP + threadIdx.x] = tot[threadIdx.x];
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_vec_a_b(int64_t n, const double* __restrict__ d,
+                                                 const double* __restrict__ Z,
+                                                 double* __restrict__ V, double* sc, double* part,
+                                                 unsigned int* counter, int first) {
+  __shared__ double tot[32];
+  const double* g = sc + B_COUNT * KP;
+  if (g[G_ALLDONE] != 0.0) return;
+  const int j = threadIdx.x % KP;
+  const double beta = sqrt(sc[B_UNORM2 * KP + j]);
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  const bool frozen = sc[B_DONE * KP + j] != 0.0;
+  double s2 = 0.0;
+  if (!frozen) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      double t = d[e / KP] * Z[e] * ib;
+      if (!first) t = __fma_rn(-beta, V[e], t);
+      V[e] = t;
+      s2 = __fma_rn(t, t, s2);
+    }
+  }
+  if (!grid_sum_kv<KP, 1>(&s2, part, counter, tot) || threadIdx.x >= KP) return;
+  // last block: plane rotation of right-hand side jj (Paige-Saunders)
+  const int jj = threadIdx.x;
+  if (jj >= (int)g[G_K] || sc[B_DONE * KP + jj] != 0.0) return;
+  const double be = sqrt(sc[B_UNORM2 * KP + jj]);
+  const double alpha = sqrt(tot[jj]);
+  if (first) {
+    sc[B_BETA * KP + jj] = be;
+    sc[B_BNORM * KP + jj] = be;
+    sc[B_ALPHA * KP + jj] = alpha;
+    sc[B_RHOBAR * KP + jj] = alpha;
+    sc[B_PHIBAR * KP + jj] = be;
+    sc[B_RNORM * KP + jj] = be;
+    sc[B_ARNORM * KP + jj] = alpha * be;
+    sc[B_COEF * KP + jj] = be > 0.0 ? -alpha / be : 0.0;
+    if (alpha * be == 0.0) {  // b_j = 0 or A^T b_j = 0: x_j = 0
+      sc[B_ISTOP * KP + jj] = 0.0;
+      sc[B_DONE * KP + jj] = 1.0;
+      sc[B_COEF * KP + jj] = 0.0;
+    }
+    return;
+  }
+  const double alpha_old = sc[B_ALPHA * KP + jj];
+  sc[B_ANORM2 * KP + jj] += alpha_old * alpha_old + be * be;
+  const double rhobar = sc[B_RHOBAR * KP + jj], phibar = sc[B_PHIBAR * KP + jj];
+  const double rho = sqrt(rhobar * rhobar + be * be);
+  const double c = rhobar / rho, s = be / rho;
+  const double theta = s * alpha;
+  sc[B_RHO * KP + jj] = rho;
+  sc[B_C * KP + jj] = c;
+  sc[B_RHOBAR * KP + jj] = -c * alpha;
+  sc[B_PHIBAR * KP + jj] = s * phibar;
+  sc[B_T1 * KP + jj] = c * phibar / rho;
+  sc[B_T2 * KP + jj] = -theta / rho;
+  sc[B_BETA * KP + jj] = be;
+  sc[B_ALPHA * KP + jj] = alpha;
+  sc[B_COEF * KP + jj] = be > 0.0 ? -alpha / be : 0.0;
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const double* __restrict__ d,
+                                                 double* __restrict__ V, double* __restrict__ W,
+                                                 double* __restrict__ XZ,
+                                                 float2* __restrict__ Vff,
+                                                 const double* __restrict__ xref, double* sc,
+                                                 double* part, unsigned int* counter, int first,
+                                                 double* err_hist) {
+  __shared__ double tot[3 * 32];
+  double* g = sc + B_COUNT * KP;
+  if (g[G_ALLDONE] != 0.0) return;
+  const int j = threadIdx.x % KP;
+  const bool frozen = sc[B_DONE * KP + j] != 0.0 || j >= (int)g[G_K];
+  const double alpha = sc[B_ALPHA * KP + j];
+  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  const double rho = first ? 1.0 : sc[B_RHO * KP + j];
+  const double irho = 1.0 / rho;
+  const double t1 = first ? 0.0 : sc[B_T1 * KP + j], t2 = first ? 0.0 : sc[B_T2 * KP + j];
+  double acc[3] = {0.0, 0.0, 0.0};  // ||d_k||^2, ||x||^2, ||x - x_ref||^2
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double dj = d[e / KP];
+    double xv;
+    if (frozen) {
+      Vff[e] = make_float2(0.f, 0.f);
+      xv = first ? 0.0 : dj * XZ[e];
+    } else {
+      const double vn = V[e] * ia;
+      if (first) {
+        W[e] = vn;
+        XZ[e] = 0.0;
+        xv = 0.0;
+      } else {
+        const double wj = W[e];
+        const double dk = wj * irho;
+        acc[0] = __fma_rn(dk, dk, acc[0]);
+        const double xn = __fma_rn(t1, wj, XZ[e]);
+        XZ[e] = xn;
+        W[e] = __fma_rn(t2, wj, vn);
+        xv = dj * xn;
+      }
+      V[e] = vn;
+      const ff f = ff_from_double(dj * vn);
+      Vff[e] = make_float2(f.h, f.l);
+    }
+    acc[1] = __fma_rn(xv, xv, acc[1]);
+    if (xref) {
+      const double ex = xv - xref[e];
+      acc[2] = __fma_rn(ex, ex, acc[2]);
+    }
+  }
+  if (!grid_sum_kv<KP, 3>(acc, part, counter, tot)) return;
+  const int K = (int)g[G_K];
+  if (first) {
+    if (threadIdx.x == 0) {
+      bool all = true;
+      for (int q = 0; q < K; ++q) all = all && sc[B_DONE * KP + q] != 0.0;
+      if (all) g[G_ALLDONE] = 1.0;
+    }
+    return;
+  }
+  const int64_t it = (int64_t)g[G_ITER];
+  const int jj = threadIdx.x;
+  if (jj < K) {
+    if (err_hist) {
+      const double xr2 = sc[B_XREF2 * KP + jj];
+      err_hist[it * K + jj] = xr2 > 0.0 ? sqrt(tot[64 + jj] / xr2) : sqrt(tot[64 + jj]);
+    }
+    if (sc[B_DONE * KP + jj] == 0.0) {
+      const double itn = sc[B_ITN * KP + jj] + 1.0;
+      sc[B_ITN * KP + jj] = itn;
+      const double ddnorm = sc[B_DDNORM * KP + jj] + tot[jj];
+      sc[B_DDNORM * KP + jj] = ddnorm;
+      const double anorm = sqrt(sc[B_ANORM2 * KP + jj]);
+      const double acond = anorm * sqrt(ddnorm);
+      const double rnorm = sc[B_PHIBAR * KP + jj];
+      const double arnorm = sc[B_ALPHA * KP + jj] * fabs(sc[B_C * KP + jj]) * rnorm;
+      const double xnorm = sqrt(tot[32 + jj]);
+      const double bnorm = sc[B_BNORM * KP + jj];
+      sc[B_ACOND * KP + jj] = acond;
+      sc[B_RNORM * KP + jj] = rnorm;
+      sc[B_ARNORM * KP + jj] = arnorm;
+      sc[B_XNORM * KP + jj] = xnorm;
+      const double atol = g[G_ATOL], btol = g[G_BTOL], ctol = g[G_CTOL];
+      const double test1 = rnorm / bnorm;
+      const double test2 = (anorm * rnorm > 0.0) ? arnorm / (anorm * rnorm) : 0.0;
+      const double test3 = 1.0 / acond;
+      const double t1n = test1 / (1.0 + anorm * xnorm / bnorm);
+      const double rtol = btol + atol * anorm * xnorm / bnorm;
+      int istop = 0;
+      if (itn >= g[G_ITNLIM]) istop = 7;
+      if (1.0 + test3 <= 1.0) istop = 6;
+      if (1.0 + test2 <= 1.0) istop = 5;
+      if (1.0 + t1n <= 1.0) istop = 4;
+      if (test3 <= ctol) istop = 3;
+      if (test2 <= atol) istop = 2;
+      if (test1 <= rtol) istop = 1;
+      sc[B_ISTOP * KP + jj] = istop;
+      if (istop != 0) {
+        sc[B_DONE * KP + jj] = 1.0;
+        sc[B_COEF * KP + jj] = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    g[G_ITER] = (double)(it + 1);
+    bool all = true;
+    for (int q = 0; q < K; ++q) all = all && sc[B_DONE * KP + q] != 0.0;
+    if (all || it + 1 >= (int64_t)g[G_ITNLIM]) g[G_ALLDONE] = 1.0;
+  }
+}
+
+// x_j = D z_j into the caller layout [n][k].
+__global__ void k_finish_b(int64_t n, int k, int KP, const double* __restrict__ d,
+                           const double* __restrict__ XZ, double* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    x[e] = d[i] * XZ[i * KP + e % k];
+  }
+}
+__global__ void k_scale_b(int64_t n, int mode, const double* __restrict__ colnorm,
+                          const double* __restrict__ user, double* __restrict__ dsc) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double s = 1.0;
+    if (mode == GSR_PRECOND_COLNORM) {
+      const double c = colnorm[j];
+      s = c > 0.0 ? 1.0 / c : 1.0;
+    } else if (mode == GSR_PRECOND_USER) {
+      s = user[j];
+    }
+    dsc[j] = s;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side: workspace, launchers, autotuner, driver.
+// ---------------------------------------------------------------------------
+struct BatchWork {
+  int KP = 0;
+  int64_t n_rows = 0, n_unk = 0;
+  float2 *U = nullptr, *Uk = nullptr, *Vff = nullptr;
+  double *V = nullptr, *W = nullptr, *XZ = nullptr, *Z = nullptr, *D = nullptr;
+  double *sc = nullptr, *hsc = nullptr, *part = nullptr;
+  unsigned int* count = nullptr;
+  int threads = 256;  // block width of the row/knot kernels (tuned)
+  int kc = 1;         // right-hand sides per instrumental block (tuned)
+  bool tuned = false;
+};
+
+static void free_batch(BatchWork* w) {
+  if (!w) return;
+  void* p[] = {w->U, w->Uk, w->Vff, w->V, w->W, w->XZ, w->Z, w->D, w->sc, w->part, w->count};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  if (w->hsc) cudaFreeHost(w->hsc);
+  delete w;
+}
+
+void destroy_batch(gsr_system* s) {
+  free_batch(static_cast<BatchWork*>(s->batch));
+  s->batch = nullptr;
+}
+
+static int kpad(int k) {
+  int p = 1;
+  while (p < k) p <<= 1;
+  return p;
+}
+
+static int batch_work(gsr_system* s, int KP, BatchWork** out) {
+  BatchWork* w = static_cast<BatchWork*>(s->batch);
+  if (w && w->KP == KP) {
+    *out = w;
+    return GSR_OK;
+  }
+  free_batch(w);
+  s->batch = nullptr;
+  w = new BatchWork();
+  w->KP = KP;
+  w->n_rows = s->L.n_rows;
+  w->n_unk = s->L.n_unk;
+  const int64_t np = padded_rows(s->L), m = s->L.n_unk;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 8);
+  };
+  A((void**)&w->U, np * KP * 8);
+  A((void**)&w->Uk, (s->L.n_rows + 1) * KP * 8);
+  A((void**)&w->Vff, m * KP * 8);
+  A((void**)&w->V, m * KP * 8);
+  A((void**)&w->W, m * KP * 8);
+  A((void**)&w->XZ, m * KP * 8);
+  A((void**)&w->Z, m * KP * 8);
+  A((void**)&w->D, m * 8);
+  A((void**)&w->sc, (B_COUNT * KP + G_COUNT) * 8);
+  A((void**)&w->part, (size_t)148 * 16 * 3 * 32 * 8);
+  A((void**)&w->count, 16 * 4);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w->hsc, (B_COUNT * KP + G_COUNT) * 8);
+  if (e == cudaSuccess) e = cudaMemset(w->U, 0, np * KP * 8);
+  if (e == cudaSuccess) e = cudaMemset(w->count, 0, 16 * 4);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(w);
+    return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
+  }
+  s->batch = w;
+  *out = w;
+  return GSR_OK;
+}
+
+static int instr_kc_max(const gsr_system* s, int KP) {
+  int kc = KP;
+  while (kc > 1 && (int64_t)(s->L.n_instr + s->L.ct_rows) * kc * 8 > INSTR_SMEM_BUDGET) kc >>= 1;
+  return kc;
+}
+
+template <int KP>
+static int launch_aprod1_bt(gsr_system* s, BatchWork* w, const float2* X, float2* Y,
+                            const double* coef, float2* Yk, double* norm_out, const double* stop,
+                            cudaStream_t st) {
+  const Layout& L = s->L;
+  if (L.n_recs <= 0) return GSR_OK;
+  const int wpb = w->threads / 32;
+  const int blocks = (int)std::min<int64_t>((L.n_recs + wpb - 1) / wpb, (int64_t)s->num_sms * 16);
+  k_aprod1_b<KP><<<blocks, w->threads, 0, st>>>(L, X, Y, coef, Yk, w->part, w->count + 0,
+                                                norm_out, stop);
+  return cuda_status(cudaGetLastError());
+}
+
+template <int KP>
+static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const float2* Yk,
+                            double* X, const double* stop, cudaStream_t st) {
+  const Layout& L = s->L;
+  if (L.n_rows <= 0) return GSR_OK;
+  if (cudaEventRecord(s->ev_fork, st) != cudaSuccess) return GSR_E_CUDA;
+  if (cudaStreamWaitEvent(s->side, s->ev_fork, 0) != cudaSuccess) return GSR_E_CUDA;
+  const int att_blocks = (L.n_att_warps + 7) / 8;
+  if (att_blocks > 0) k_aprod2_att_b<KP><<<att_blocks, 256, 0, s->side>>>(L, Yk, X, stop);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  const int kc = std::min(w->kc, instr_kc_max(s, KP));
+  const int chunks = KP / kc;
+  const int groups = std::max(1, (int)std::min<int64_t>(L.n_ctiles, s->num_sms / chunks > 0 ?
+                                                                      s->num_sms / chunks : 1));
+  const int ismem = (int)((L.n_instr + L.ct_rows) * kc * 8);
+  if (L.n_ctiles > 0)
+    k_aprod2_instr_b<KP><<<groups * chunks, 512, ismem, st>>>(L, Y, X, groups, kc, stop);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  const int wpb = w->threads / 32;
+  const int ab = (int)std::min<int64_t>((L.n_recs + wpb - 1) / wpb, (int64_t)s->num_sms * 16);
+  k_aprod2_astro_b<KP><<<ab, w->threads, 0, st>>>(L, Y, X, stop);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  if (cudaEventRecord(s->ev_join, s->side) != cudaSuccess) return GSR_E_CUDA;
+  if (cudaStreamWaitEvent(st, s->ev_join, 0) != cudaSuccess) return GSR_E_CUDA;
+  return GSR_OK;
+}
+
+#define GSR_KP_DISPATCH(KPV, CALL)                 \
+  switch (KPV) {                                   \
+    case 1: { constexpr int KP = 1; return CALL; } \
+    case 2: { constexpr int KP = 2; return CALL; } \
+    case 4: { constexpr int KP = 4; return CALL; } \
+    case 8: { constexpr int KP = 8; return CALL; } \
+    case 16: { constexpr int KP = 16; return CALL; } \
+    case 32: { constexpr int KP = 32; return CALL; } \
+    default: return GSR_E_ARG;                     \
+  }
+
+static int aprod1_b(gsr_system* s, BatchWork* w, const float2* X, float2* Y, const double* coef,
+                    float2* Yk, double* norm_out, const double* stop, cudaStream_t st) {
+  GSR_KP_DISPATCH(w->KP, (launch_aprod1_bt<KP>(s, w, X, Y, coef, Yk, norm_out, stop, st)));
+}
+static int aprod2_b(gsr_system* s, BatchWork* w, const float2* Y, const float2* Yk, double* X,
+                    const double* stop, cudaStream_t st) {
+  GSR_KP_DISPATCH(w->KP, (launch_aprod2_bt<KP>(s, w, Y, Yk, X, stop, st)));
+}
+
+static int set_batch_attributes() {
+  static bool done = false;
+  if (done) return GSR_OK;
+  cudaError_t e = cudaSuccess;
+#define GSR_SETATTR(KPV)                                                                     \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_aprod2_instr_b<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             INSTR_SMEM_BUDGET);
+  GSR_SETATTR(1) GSR_SETATTR(2) GSR_SETATTR(4) GSR_SETATTR(8) GSR_SETATTR(16) GSR_SETATTR(32)
+#undef GSR_SETATTR
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  done = true;
+  return GSR_OK;
+}
+
+// The autotuner: times aprod 1 + aprod 2 for every (block width, instrumental
+// chunk) candidate on the system's own data and keeps the fastest.
+static int autotune(gsr_system* s, BatchWork* w, cudaStream_t st) {
+  if (w->tuned) return GSR_OK;
+  const int widths[] = {128, 256};
+  std::vector<int> kcs;
+  for (int kc = instr_kc_max(s, w->KP); kc >= 1; kc >>= 1) kcs.push_back(kc);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GSR_E_CUDA;
+  float best = 1e30f;
+  int bw = 256, bkc = kcs.empty() ? 1 : kcs[0];
+  for (int width : widths) {
+    for (int kc : kcs) {
+      w->threads = width;
+      w->kc = kc;
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaMemsetAsync(w->Z, 0, w->n_unk * w->KP * 8, st);
+        cudaEventRecord(e0, st);
+        int rc = aprod1_b(s, w, w->Vff, w->U, nullptr, nullptr, nullptr, nullptr, st);
+        if (rc == GSR_OK) rc = aprod2_b(s, w, w->U, w->Uk, w->Z, nullptr, st);
+        cudaEventRecord(e1, st);
+        if (rc != GSR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return GSR_E_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t_min = std::min(t_min, ms);
+      }
+      if (t_min < best) {
+        best = t_min;
+        bw = width;
+        bkc = kc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  w->threads = bw;
+  w->kc = bkc;
+  w->tuned = true;
+  return GSR_OK;
+}
+
+template <int KP>
+static int enqueue_b(gsr_system* s, BatchWork* w, const double* xref, double* err_dev,
+                     cudaStream_t st, int first) {
+  const int64_t m = s->L.n_unk;
+  double* stop = w->sc + B_COUNT * KP + G_ALLDONE;
+  const int vb = (int)std::min<int64_t>((m * KP + 255) / 256, (int64_t)s->num_sms * 8);
+  int rc = GSR_OK;
+  if (!first) {
+    rc = aprod1_b(s, w, w->Vff, w->U, w->sc + B_COEF * KP, w->Uk, w->sc + B_UNORM2 * KP, stop, st);
+    if (rc != GSR_OK) return rc;
+  }
+  k_zero_d<<<vb, 256, 0, st>>>(w->Z, m * KP, first ? nullptr : stop);
+  rc = aprod2_b(s, w, w->U, w->Uk, w->Z, first ? nullptr : stop, st);
+  if (rc != GSR_OK) return rc;
+  k_vec_a_b<KP><<<vb, 256, 0, st>>>(m, w->D, w->Z, w->V, w->sc, w->part, w->count + 1, first);
+  k_vec_b_b<KP><<<vb, 256, 0, st>>>(m, w->D, w->V, w->W, w->XZ, w->Vff, first ? nullptr : xref,
+                                    w->sc, w->part, w->count + 2, first, first ? nullptr : err_dev);
+  return cuda_status(cudaGetLastError());
+}
+static int enqueue_iter_b(gsr_system* s, BatchWork* w, const double* xref, double* err_dev,
+                          cudaStream_t st, int first) {
+  GSR_KP_DISPATCH(w->KP, (enqueue_b<KP>(s, w, xref, err_dev, st, first)));
+}
+template <int KP>
+static int init_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
+                  cudaStream_t st) {
+  const int64_t rb = std::min<int64_t>((s->L.n_rows * KP + 255) / 256, (int64_t)s->num_sms * 8);
+  k_init_b<KP><<<(int)std::max<int64_t>(rb, 1), 256, 0, st>>>(s->L, B, k, w->U, w->Uk, w->sc,
+                                                              w->part, w->count + 3);
+  if (xref) {
+    const int vb = (int)std::min<int64_t>((s->L.n_unk * KP + 255) / 256, (int64_t)s->num_sms * 8);
+    k_xref2_b<KP><<<vb, 256, 0, st>>>(s->L.n_unk, xref, w->sc, w->part, w->count + 4);
+  }
+  return cuda_status(cudaGetLastError());
+}
+static int init_iter_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
+                       cudaStream_t st) {
+  GSR_KP_DISPATCH(w->KP, (init_b<KP>(s, w, B, k, xref, st)));
+}
+
+__global__ void k_pack_xref(const double* __restrict__ in, int k, int KP, int64_t n,
+                            double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % KP);
+    out[e] = j < k ? in[(e / KP) * k + j] : 0.0;
+  }
+}
+
+int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_opts* o,
+               gsr_lsqr_result* res, cudaStream_t st) {
+  const int KP = kpad(k);
+  BatchWork* w = nullptr;
+  int rc = batch_work(s, KP, &w);
+  if (rc != GSR_OK) return rc;
+  if ((rc = set_batch_attributes()) != GSR_OK) return rc;
+  const int64_t m = s->L.n_unk;
+  const int64_t itnlim = o->itnlim > 0 ? o->itnlim : 20 * std::max<int64_t>(1, m);
+  cudaError_t e = cudaSuccess;
+  auto C = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  const int vb = (int)std::min<int64_t>((m + 255) / 256, (int64_t)s->num_sms * 8);
+  k_scale_b<<<vb, 256, 0, st>>>(m, o->precond, s->colnorm, o->scale, w->D);
+  // the autotuner runs once per system and k, on the (so far unused) work vectors
+  if (!w->tuned) {
+    C(cudaMemsetAsync(w->Vff, 0, m * KP * 8, st));
+    C(cudaMemsetAsync(w->Uk, 0, s->L.n_rows * KP * 8, st));
+    if ((rc = autotune(s, w, st)) != GSR_OK) return rc;
+  }
+  std::vector<double> h(B_COUNT * KP + G_COUNT, 0.0);
+  double* g = h.data() + B_COUNT * KP;
+  g[G_ATOL] = o->atol;
+  g[G_BTOL] = o->btol;
+  g[G_CTOL] = o->conlim > 0.0 ? 1.0 / o->conlim : 0.0;
+  g[G_ITNLIM] = (double)itnlim;
+  g[G_K] = k;
+  for (int j = k; j < KP; ++j) h[B_DONE * KP + j] = 1.0;  // padding lanes never run
+  C(cudaMemcpyAsync(w->sc, h.data(), h.size() * 8, cudaMemcpyHostToDevice, st));
+  C(cudaStreamSynchronize(st));
+  double* xref = nullptr;
+  double* err_dev = nullptr;
+  if (o->x_ref && o->err_hist) {
+    C(cudaMallocAsync((void**)&xref, m * KP * 8, st));
+    C(cudaMallocAsync((void**)&err_dev, (itnlim + 1) * k * 8, st));
+    if (e != cudaSuccess) return GSR_E_CUDA;
+    k_pack_xref<<<vb, 256, 0, st>>>(o->x_ref, k, KP, m, xref);
+  }
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  rc = init_iter_b(s, w, B, k, xref, st);
+  if (rc == GSR_OK) rc = enqueue_iter_b(s, w, xref, err_dev, st, 1);
+  if (rc != GSR_OK) return rc;
+  int64_t n_launches = 11;
+  // iterations: graph of a chunk of iterations, replayed until every RHS stopped
+  const int chunk = 4;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = st != nullptr;
+  if (use_graph) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      use_graph = false;
+  }
+  if (use_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    int r2 = GSR_OK;
+    for (int i = 0; i < chunk && r2 == GSR_OK; ++i) r2 = enqueue_iter_b(s, w, xref, err_dev, st, 0);
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (r2 != GSR_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      graph = nullptr;
+      exec = nullptr;
+      use_graph = false;
+    }
+  } else {
+    cudaGetLastError();
+    use_graph = false;
+  }
+  const size_t hbytes = (B_COUNT * KP + G_COUNT) * 8;
+  int64_t launched = 0;
+  while (true) {
+    if (use_graph) {
+      C(cudaGraphLaunch(exec, st));
+    } else {
+      for (int i = 0; i < chunk && rc == GSR_OK; ++i) rc = enqueue_iter_b(s, w, xref, err_dev, st, 0);
+    }
+    launched += chunk;
+    n_launches += (int64_t)chunk * 8;
+    C(cudaMemcpyAsync(w->hsc, w->sc, hbytes, cudaMemcpyDeviceToHost, st));
+    C(cudaStreamSynchronize(st));
+    if (e != cudaSuccess || rc != GSR_OK) break;
+    if (w->hsc[B_COUNT * KP + G_ALLDONE] != 0.0) break;
+    if (launched > itnlim + chunk) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || rc != GSR_OK) {
+    if (xref) cudaFreeAsync(xref, st);
+    if (err_dev) cudaFreeAsync(err_dev, st);
+    return rc != GSR_OK ? rc : GSR_E_CUDA;
+  }
+  k_finish_b<<<vb, 256, 0, st>>>(m, k, KP, w->D, w->XZ, X);
+  const int64_t iters = (int64_t)w->hsc[B_COUNT * KP + G_ITER];
+  if (o->err_hist && err_dev && iters > 0)
+    C(cudaMemcpyAsync(o->err_hist, err_dev, iters * k * 8, cudaMemcpyDeviceToHost, st));
+  if (xref) C(cudaFreeAsync(xref, st));
+  if (err_dev) C(cudaFreeAsync(err_dev, st));
+  C(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  const double* hs = w->hsc;
+  for (int j = 0; j < k; ++j) {
+    gsr_lsqr_result& r = res[j];
+    std::memset(&r, 0, sizeof(r));
+    r.istop = (int32_t)hs[B_ISTOP * KP + j];
+    r.itn = (int64_t)hs[B_ITN * KP + j];
+    r.rnorm = hs[B_RNORM * KP + j];
+    r.arnorm = hs[B_ARNORM * KP + j];
+    r.anorm = std::sqrt(hs[B_ANORM2 * KP + j]);
+    r.acond = hs[B_ACOND * KP + j];
+    r.xnorm = hs[B_XNORM * KP + j];
+    r.n_launches = n_launches;
+    r.n_timed_itn = iters;
+  }
+  return GSR_OK;
+}
+
+}  // namespace gsr
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* stream) {
+  if (!sys || k < 1 || k > 32 || (!X && sys->L.n_unk > 0) || (!Y && sys->L.n_rows > 0))
+    return GSR_E_ARG;
+  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int KP = gsr::kpad(k);
+  gsr::BatchWork* w = nullptr;
+  int rc = gsr::batch_work(sys, KP, &w);
+  if (rc != GSR_OK) return rc;
+  const int64_t m = sys->L.n_unk, n = sys->L.n_rows;
+  const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
+  const int bn = (int)std::min<int64_t>((n * KP + 255) / 256 + 1, sys->num_sms * 8);
+  gsr::k_pack_ff<<<bm, 256, 0, st>>>(X, k, KP, m, w->Vff);
+  gsr::k_pack_ff<<<bn, 256, 0, st>>>(Y, k, KP, n, w->U);
+  rc = gsr::aprod1_b(sys, w, w->Vff, w->U, nullptr, nullptr, nullptr, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  gsr::k_unpack_ff<<<bn, 256, 0, st>>>(w->U, k, KP, n, Y);
+  return gsr::cuda_status(cudaGetLastError());
+}
+
+int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* stream) {
+  if (!sys || k < 1 || k > 32 || (!X && sys->L.n_unk > 0) || (!Y && sys->L.n_rows > 0))
+    return GSR_E_ARG;
+  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int KP = gsr::kpad(k);
+  gsr::BatchWork* w = nullptr;
+  int rc = gsr::batch_work(sys, KP, &w);
+  if (rc != GSR_OK) return rc;
+  if ((rc = gsr::set_batch_attributes()) != GSR_OK) return rc;
+  const int64_t m = sys->L.n_unk;
+  const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
+  const int bn = (int)std::min<int64_t>((sys->L.n_rows * KP + 255) / 256 + 1, sys->num_sms * 8);
+  gsr::k_pack_ff_knot<<<bn, 256, 0, st>>>(sys->L, Y, k, KP, w->U, w->Uk);
+  gsr::k_zero_d<<<bm, 256, 0, st>>>(w->Z, m * KP, nullptr);
+  rc = gsr::aprod2_b(sys, w, w->U, w->Uk, w->Z, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  gsr::k_add_cols<<<bm, 256, 0, st>>>(w->Z, k, KP, m, X);
+  return gsr::cuda_status(cudaGetLastError());
+}
+
+int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
+                         const gsr_lsqr_opts* opts, gsr_lsqr_result* res, void* stream) {
+  if (!sys || !opts || !res || k < 1 || k > 32) return GSR_E_ARG;
+  if ((!B && sys->L.n_rows > 0) || (!X && sys->L.n_unk > 0)) return GSR_E_ARG;
+  if (opts->precond < GSR_PRECOND_NONE || opts->precond > GSR_PRECOND_USER) return GSR_E_ARG;
+  if (opts->precond == GSR_PRECOND_USER && !opts->scale) return GSR_E_ARG;
+  if (opts->precision != GSR_PREC_F64 || opts->var || opts->rnorm_hist) return GSR_E_UNSUPPORTED;
+  if (opts->err_hist && !opts->x_ref) return GSR_E_ARG;
+  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (sys->L.n_rows == 0 || sys->L.n_unk == 0) {
+    if (X && sys->L.n_unk > 0) cudaMemsetAsync(X, 0, sys->L.n_unk * k * 8, st);
+    for (int j = 0; j < k; ++j) std::memset(&res[j], 0, sizeof(res[j]));
+    return gsr::cuda_status(cudaStreamSynchronize(st));
+  }
+  return gsr::lsqr_batch(sys, k, B, X, opts, res, st);
+}
+
+int gsr_batch_tuning(const gsr_system* sys, int* threads, int* kc) {
+  if (!sys || !sys->batch) return GSR_E_ARG;
+  const gsr::BatchWork* w = static_cast<const gsr::BatchWork*>(sys->batch);
+  if (threads) *threads = w->threads;
+  if (kc) *kc = w->kc;
+  return GSR_OK;
+}
+
+}  // extern "C"

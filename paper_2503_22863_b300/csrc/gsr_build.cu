@@ -112,6 +112,7 @@ int dalloc(T** p, size_t count) {
 
 void free_system(gsr_system* s) {
   if (!s) return;
+  destroy_batch(s);
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
                   s->att_warp_knot, s->ct_round, s->round_entry, s->ient_ff, s->ient_f32,
                   s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,

@@ -268,6 +268,7 @@ struct gsr_system {
   double* mx_r;          // mixed precision: residual b - A x1 [n_rows]
   double* scal;          // device LSQR scalars
   double* host_scal;     // pinned mirror of scal
+  void* batch;           // multi-right-hand-side workspace (allocated on first use)
   cudaStream_t side;     // second stream for the attitude part of aprod 2
   cudaEvent_t ev_fork, ev_join;
   int main_block, main_ctas, main_smem;
@@ -312,4 +313,5 @@ int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_
                       cudaStream_t st);
 int cuda_status(cudaError_t e);
 int set_kernel_attributes();
+void destroy_batch(gsr_system* s);
 }  // namespace gsr

@@ -83,6 +83,16 @@ def _load():
     lib.gsr_lsqr_solve.argtypes = [_c_p, _c_p, _c_p, ctypes.POINTER(LsqrOpts),
                                    ctypes.POINTER(LsqrResult), _c_p]
     lib.gsr_lsqr_solve.restype = ctypes.c_int
+    for name in ("gsr_aprod1_batch", "gsr_aprod2_batch"):
+        getattr(lib, name).argtypes = [_c_p, ctypes.c_int, _c_p, _c_p, _c_p]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.gsr_lsqr_solve_batch.argtypes = [_c_p, ctypes.c_int, _c_p, _c_p,
+                                         ctypes.POINTER(LsqrOpts), ctypes.POINTER(LsqrResult),
+                                         _c_p]
+    lib.gsr_lsqr_solve_batch.restype = ctypes.c_int
+    lib.gsr_batch_tuning.argtypes = [_c_p, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+    lib.gsr_batch_tuning.restype = ctypes.c_int
     return lib
 
 
@@ -219,3 +229,73 @@ class System:
         if rh is not None:
             out["rnorm_hist"] = rh[:r.itn]
         return out
+
+
+def _dptr2(t, n, k, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (n, k):
+        raise ValueError("%s must be a contiguous float64 tensor of shape (%d, %d)" % (name, n, k))
+    return _c_p(t.data_ptr())
+
+
+def _batch_methods():
+    def aprod1_batch(self, X, Y):
+        """Eq. 2 for k columns: Y[n_rows, k] += A X[N_unk, k]."""
+        k = int(X.shape[1])
+        _check(lib.gsr_aprod1_batch(self._h, k, _dptr2(X, self.n_unk, k, "X"),
+                                    _dptr2(Y, self.n_rows, k, "Y"), _stream()), "gsr_aprod1_batch")
+        return Y
+
+    def aprod2_batch(self, Y, X):
+        """Eq. 3 for k columns: X[N_unk, k] += A^T Y[n_rows, k]."""
+        k = int(Y.shape[1])
+        _check(lib.gsr_aprod2_batch(self._h, k, _dptr2(Y, self.n_rows, k, "Y"),
+                                    _dptr2(X, self.n_unk, k, "X"), _stream()), "gsr_aprod2_batch")
+        return X
+
+    def lsqr_batch(self, B, X=None, atol=1e-12, btol=1e-12, conlim=1e12, itnlim=0,
+                   precond="colnorm", scale=None, x_ref=None, err_hist=False):
+        """LSQR on k right-hand sides B[n_rows, k] at once (gsr_lsqr_solve_batch)."""
+        k = int(B.shape[1])
+        o = LsqrOpts()
+        lib.gsr_lsqr_default_opts(ctypes.byref(o))
+        o.atol, o.btol, o.conlim, o.itnlim = atol, btol, conlim, int(itnlim)
+        o.precond = PRECOND[precond]
+        if scale is not None:
+            o.scale = _dptr(scale, self.n_unk, "scale").value
+        eh = None
+        lim = int(itnlim) if itnlim else 20 * max(1, self.n_unk)
+        if x_ref is not None:
+            o.x_ref = _dptr2(x_ref, self.n_unk, k, "x_ref").value
+        if err_hist:
+            if x_ref is None:
+                raise ValueError("err_hist needs x_ref")
+            eh = np.full((lim + 1) * k, np.nan)
+            o.err_hist = eh.ctypes.data
+        if X is None:
+            X = torch.empty((self.n_unk, k), dtype=torch.float64, device=self.device)
+        res = (LsqrResult * k)()
+        _check(lib.gsr_lsqr_solve_batch(self._h, k, _dptr2(B, self.n_rows, k, "B"),
+                                        _dptr2(X, self.n_unk, k, "X"), ctypes.byref(o), res,
+                                        _stream()), "gsr_lsqr_solve_batch")
+        out = dict(x=X, istop=[r.istop for r in res], itn=[r.itn for r in res],
+                   rnorm=[r.rnorm for r in res], anorm=[r.anorm for r in res],
+                   iterations=res[0].n_timed_itn, n_launches=res[0].n_launches)
+        if eh is not None:
+            it = res[0].n_timed_itn
+            out["err_hist"] = eh[:it * k].reshape(it, k)
+        return out
+
+    def batch_tuning(self):
+        t, c = ctypes.c_int(), ctypes.c_int()
+        _check(lib.gsr_batch_tuning(self._h, ctypes.byref(t), ctypes.byref(c)), "gsr_batch_tuning")
+        return dict(threads=t.value, kc=c.value)
+
+    System.aprod1_batch = aprod1_batch
+    System.aprod2_batch = aprod2_batch
+    System.lsqr_batch = lsqr_batch
+    System.batch_tuning = batch_tuning
+
+
+_batch_methods()
