@@ -33,18 +33,19 @@ METRIC = "LSQR time-to-1e-9 and aprod1/aprod2 HBM GB/s vs peak: FP64 vs mixed/ba
 TARGET_ERR = 1e-9
 # Iterations to 1e-9 on the medium workload, measured by this benchmark's own
 # N* search (used by the CPU reference arm, which cannot afford to find N*).
-MEDIUM_ITERS_TO_1E9 = 40
+MEDIUM_ITERS_TO_1E9 = 68
 FALLBACK_HBM_GBS = 6400.0
 # Algorithmic bytes of one launch group, per row and per unknown, for the
-# device layout (float-pair values, 32-bit star/knot/position indices and
-# 16-bit instrumental indices):
-#   aprod 1: 24 values x 8 B + 4 star + 4 knot + 12 instr + 4 knot position
-#            + 8 u read + 8 u write + 8 u scatter to knot order = 240 B/row;
-#            x gathered once (8 B/unknown) + zeroing of z (8 B/unknown)
-#   aprod 2: star-ordered part 40 astro + 8 glob + 48 instr + 12 instr idx
-#            + 4 star + 8 u = 120 B/row; knot-ordered part 96 att + 8 u = 104 B/row;
-#            z read-modify-write 16 B/unknown
-BYTES = {"aprod1": (240, 16), "aprod2": (224, 16)}
+# FP64 method: a row is 24 FP64 values + 8 B star offset + 8 B attitude offset
+# + 6 x 4 B instrumental columns = 232 B.
+#   aprod 1 (u = A v - alpha u): 232 A + 8 u read + 8 u write = 248 B/row;
+#            v read once = 8 B/unknown
+#   aprod 2 (v = A^T u - beta v): 232 A + 8 u = 240 B/row; v read + write
+#            = 16 B/unknown
+# (The device layout moves 240 B/row in aprod 1 and 244 B/row in aprod 2:
+# float-pair values are 8 B like FP64, indices are narrower, and the row order
+# and knot order copies add a u scatter and a second u read.)
+BYTES = {"aprod1": (248, 8), "aprod2": (240, 16)}
 
 
 def log(*a):
@@ -284,6 +285,85 @@ def bench_batched(S, sys_, k, ms_single, args, stream, dev):
             "gpu_launches": int(res["n_launches"]) * steps}
 
 
+def bench_learned(args, dev):
+    """Learned column preconditioner on its family of 64 seeded systems
+    (200,000 stars x max(Poisson(30), 5) obs, K log-uniform on [5k, 50k],
+    n_instr on [500, 5000]): labels from solve histories on systems 0-39,
+    the fallback gate on 40-47, iterations to 1e-9 on the held-out 48-63,
+    learned vs plain column scaling. Systems are generated one ahead on a
+    host thread while the GPU works on the current one."""
+    import threading
+    import torch
+    from paper_2503_22863_b300 import gsr, learned, synth
+
+    def gen(s, out):
+        out[s] = synth.make_system(**synth.learned_system_params(s))
+
+    n_sys = args.learned_systems
+    n_train, n_val = (n_sys * 40) // 64, (n_sys * 8) // 64
+    pending = {}
+    th = threading.Thread(target=gen, args=(0, pending))
+    th.start()
+    feats, labels, val, held = [], [], [], []
+    t_lab = t_eval = 0.0
+    gam = []
+    for s in range(n_sys):
+        th.join()
+        sys_ = pending.pop(s)
+        if s + 1 < n_sys:
+            th = threading.Thread(target=gen, args=(s + 1, pending))
+            th.start()
+        S = gsr.System(sys_, device=dev.index or 0)
+        b = learned.make_rhs(S, sys_)
+        del sys_
+        t0 = time.perf_counter()
+        probe = learned.SolveProbe(S, b, tol=TARGET_ERR)
+        if s < n_train:
+            lab, info = learned.block_labels(S, probe)
+            feats.append(S.column_features())
+            labels.append(lab)
+            gam.append((info["log2_gamma_att"], info["log2_gamma_instr"]))
+            S.close()
+            t_lab += time.perf_counter() - t0
+        elif s < n_train + n_val:
+            val.append((S, probe))
+        else:
+            held.append((S, probe))
+    t0 = time.perf_counter()
+    model, hist = learned.train(feats, labels, steps=1500, lr=2e-3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    pre = learned.LearnedPreconditioner(model)
+    pre.validate(val)
+    t0 = time.perf_counter()
+    base, raw, used = [], [], []
+    was = pre.enabled
+    for S, probe in held:
+        base.append(probe.n_colnorm)
+        pre.enabled = True
+        raw.append(probe.iterations(pre.scaling(S)))
+        pre.enabled = was
+        used.append(probe.iterations(pre.scaling(S)))
+    t_eval = time.perf_counter() - t0
+    for S, _ in val + held:
+        S.close()
+    med = lambda v: float(np.median(v))
+    log("learned: held-out median iterations colnorm %.1f, learned %.1f, with fallback %.1f "
+        "(model %s); labels %.1f s, training %.1f s (loss %.3g -> %.3g)"
+        % (med(base), med(raw), med(used), "kept" if was else "rejected by the gate", t_lab,
+           t_train, hist[0], hist[-1]))
+    return {"value": med(used), "unit": "iterations to 1e-9 (median, held-out)",
+            "systems": {"train": n_train, "validate": n_val, "held_out": len(held)},
+            "median_itn_colnorm": med(base), "median_itn_learned": med(raw),
+            "median_itn_with_fallback": med(used), "model_enabled": bool(was),
+            "validation": pre.validation, "held_out_itn_colnorm": base,
+            "held_out_itn_learned": raw,
+            "label_log2_gamma_att_range": [min(g[0] for g in gam), max(g[0] for g in gam)],
+            "label_log2_gamma_instr_range": [min(g[1] for g in gam), max(g[1] for g in gam)],
+            "train_loss_first_last": [float(hist[0]), float(hist[-1])],
+            "train_s": t_train, "label_search_s": t_lab, "eval_s": t_eval}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,6 +448,8 @@ def run_ours(args):
             for kk in args.batch_k:
                 variants["batched_k%d" % kk] = bench_batched(S, sys_, kk, ms_single=float(
                     np.mean(step_ms)), args=args, stream=stream, dev=dev)
+            if args.learned_systems > 0:
+                variants["learned"] = bench_learned(args, dev)
 
     ms = float(np.mean(step_ms))
     if dist is not None:
@@ -440,6 +522,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision / batched variants")
+    ap.add_argument("--learned-systems", type=int, default=64,
+                    help="systems of the learned-preconditioner family (40/64 train, 8/64 "
+                         "validate, the rest held out); 0 skips the variant")
     ap.add_argument("--batch-k", type=int, nargs="*", default=[8, 32],
                     help="right-hand-side counts of the batched variant")
     args = ap.parse_args()

@@ -187,13 +187,74 @@ int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* s
  * opts.err_hist (host, [itnlim][k]) with opts.x_ref (device [N_unk][k]) gives
  * per-iteration relative errors. precision must be F64; var and rnorm_hist are
  * not available here (GSR_E_UNSUPPORTED). The first call for a given k times
- * the candidate block widths and instrumental chunk sizes on this system and
+ * the candidate block widths and instrumental row-tile heights on this system and
  * keeps the fastest (gsr_batch_tuning reports the choice). Synchronous.
  */
 int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
                          const gsr_lsqr_opts* opts, gsr_lsqr_result* res, void* stream);
-/* Block width and right-hand sides per instrumental block chosen by the tuner. */
-int gsr_batch_tuning(const gsr_system* sys, int* threads, int* kc);
+/* Block width of the row kernels and row-tile height of the instrumental
+ * buckets chosen by the tuner. */
+int gsr_batch_tuning(const gsr_system* sys, int* threads, int* tile_rows);
+
+/*
+ * Learned column preconditioner (an extension: the paper scales columns by
+ * their norms only, Sec. 2). The attitude and instrumental columns,
+ * q in [0, 3K + n_instr) (global column 5 n_stars + q), each get 8 features;
+ * an MLP 8 -> 64 -> 64 -> 1 maps the standardised features to a log
+ * multiplier m_q and the column scaling becomes d_j = exp(m_q) / ||A_:,j||.
+ * LSQR converges to the same least-squares solution under any positive
+ * scaling, so this changes only the number of iterations.
+ *
+ * Parameters theta (FP32, device, GSR_MLP_NPARAM floats) are laid out as
+ * W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3:
+ *   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), m = w3 . h2 + b3.
+ * The kernels round weights, inputs and activations (and the activation
+ * gradients) to BF16 and multiply on the tensor cores with FP32 accumulation.
+ * norm (device, 16 floats) = mean[8], 1/std[8]: f_std = (f - mean) * (1/std).
+ * These calls run on the current CUDA device and are stream-ordered.
+ */
+#define GSR_MLP_NFEAT 8
+#define GSR_MLP_HIDDEN 64
+#define GSR_MLP_NPARAM 4801
+#define GSR_MLP_GRID 296 /* most blocks gsr_mlp_grad launches */
+#define GSR_MLP_WORK_FLOATS (GSR_MLP_GRID * (GSR_MLP_NPARAM + 1))
+
+/* Number of learned columns, 3K + n_instr. */
+int64_t gsr_n_learned_cols(const gsr_system* sys);
+/*
+ * feats (device, [3K + n_instr][8] row-major float) per column q with n_q the
+ * number of rows that have a coefficient slot in the column and c_q its norm:
+ *   0 log c_q (0 if c_q = 0)     4 knot / (K-1) or instrument / (n_instr-1)
+ *   1 log(1 + n_q)               5 log of the block's mean count (4 n_rows/K or 6 n_rows/n_instr)
+ *   2 1 if instrumental, else 0  6 log(1 + n_q) - log(1 + block mean count)
+ *   3 axis / 2 (0 for instr)     7 log c_q - log(max(n_q, 1)) / 2
+ * The first call also builds the per-instrument counts (library-owned).
+ */
+int gsr_column_features(gsr_system* sys, float* feats, void* stream);
+/* acc[k] += sum_i f[i][k], acc[8 + k] += sum_i f[i][k]^2 (device double[16];
+ * atomics, so the order of the additions is not fixed). */
+int gsr_feature_moments(const float* feats, int64_t n, double* acc, void* stream);
+/* m[i] = network output for feature row i (device [n]). */
+int gsr_mlp_forward(const float* feats, int64_t n, const float* norm, const float* theta,
+                    float* m, void* stream);
+/*
+ * grad = dL/dtheta of L = (1/n) sum_i (m_i - target_i)^2 and *loss = L
+ * (loss may be NULL). work is device scratch of GSR_MLP_WORK_FLOATS floats.
+ * Deterministic: per-block partial gradients are added in block order.
+ */
+int gsr_mlp_grad(const float* feats, const float* target, int64_t n, const float* norm,
+                 const float* theta, float* work, float* grad, float* loss, void* stream);
+/* One Adam step (Kingma & Ba) on theta with moments mom, vel (device,
+ * NPARAM floats each, zero before step 1); step counts from 1. */
+int gsr_mlp_adam(float* theta, const float* grad, float* mom, float* vel, int64_t step, float lr,
+                 float beta1, float beta2, float eps, void* stream);
+/*
+ * d (device [N_unk]): exp(min(max(m_q, -clamp), clamp)) / ||A_:,j|| on the
+ * learned columns, 1 / ||A_:,j|| on the others, 1 for an empty column. m
+ * NULL gives plain column scaling. Pass d to gsr_lsqr_solve with
+ * precond = GSR_PRECOND_USER.
+ */
+int gsr_learned_scaling(gsr_system* sys, const float* m, float clamp, double* d, void* stream);
 
 #ifdef __cplusplus
 }

@@ -124,36 +124,63 @@ __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __rest
   ff nrm = ff_zero();
   for (int64_t r = gw; r < L.n_recs; r += nw) {
     const unsigned char* rec = L.rec_ff + r * Rec<false>::BYTES;
+    // The record's column indices, two rows per lane, loaded up front so the
+    // x gathers of a row wait for a shuffle rather than a load: register h of
+    // lane (q, p) holds row q * RPS + h * KP + p (RPS = 2 KP), so at step
+    // (h, p) every stream reads register h of lane q * KP + p.
+    int pst[2], psk[2], ppos[2], pin[2][3];  // instrumental indices packed in pairs
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rr = q * RPS + h * KP + j;
+      pst[h] = ri(rec, Rec<false>::STAR, rr);
+      psk[h] = ri(rec, Rec<false>::ATT_S, rr);
+      ppos[h] = Yk ? ri(rec, Rec<false>::POS, rr) : 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        pin[h][k] = rinstr(rec, 2 * k, rr) | (rinstr(rec, 2 * k + 1, rr) << 16);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
 #pragma unroll 2
-    for (int i = 0; i < RPS; ++i) {
-      const int r_in = q * RPS + i;
-      const int64_t row = r * REC_ROWS + r_in;
-      if (row >= L.n_rows) break;
-      const int st = ri(rec, Rec<false>::STAR, r_in);
-      const int sk = ri(rec, Rec<false>::ATT_S, r_in);
-      ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero(), a4 = ff_zero();
+      for (int p = 0; p < KP; ++p) {
+        const int src = q * KP + p;
+        const int r_in = q * RPS + h * KP + p;
+        const int64_t row = r * REC_ROWS + r_in;
+        const int st = __shfl_sync(0xffffffffu, pst[h], src);
+        const int sk = __shfl_sync(0xffffffffu, psk[h], src);
+        const int pos = __shfl_sync(0xffffffffu, ppos[h], src);
+        int ins[6];
 #pragma unroll
-      for (int t = 0; t < 5; ++t)
-        a0 = ff_add(a0, ff_mul(rv(rec, t, r_in), ldf(X + (5 * (int64_t)st + t) * KP + j)));
+        for (int k = 0; k < 3; ++k) {
+          const int v = __shfl_sync(0xffffffffu, pin[h][k], src);
+          ins[2 * k] = v & 0xffff;
+          ins[2 * k + 1] = (int)((unsigned)v >> 16);
+        }
+        if (row >= L.n_rows) continue;  // padding rows of the last record
+        ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero(), a4 = ff_zero();
 #pragma unroll
-      for (int i4 = 0; i4 < 4; ++i4) {
-        a1 = ff_add(a1, ff_mul(rv(rec, 5 + i4, r_in), ldf(X + (L.att_base + sk + i4) * KP + j)));
-        a2 = ff_add(a2, ff_mul(rv(rec, 9 + i4, r_in),
-                               ldf(X + (L.att_base + K + sk + i4) * KP + j)));
-        a3 = ff_add(a3, ff_mul(rv(rec, 13 + i4, r_in),
-                               ldf(X + (L.att_base + 2 * K + sk + i4) * KP + j)));
+        for (int t = 0; t < 5; ++t)
+          a0 = ff_add(a0, ff_mul(rv(rec, t, r_in), ldf(X + (5 * (int64_t)st + t) * KP + j)));
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+          a1 = ff_add(a1,
+                      ff_mul(rv(rec, 5 + i4, r_in), ldf(X + (L.att_base + sk + i4) * KP + j)));
+          a2 = ff_add(a2, ff_mul(rv(rec, 9 + i4, r_in),
+                                 ldf(X + (L.att_base + K + sk + i4) * KP + j)));
+          a3 = ff_add(a3, ff_mul(rv(rec, 13 + i4, r_in),
+                                 ldf(X + (L.att_base + 2 * K + sk + i4) * KP + j)));
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          a4 = ff_add(a4, ff_mul(rv(rec, 17 + k, r_in), ldf(X + (L.instr_base + ins[k]) * KP + j)));
+        if (glob) a4 = ff_add(a4, ff_mul(rv(rec, 23, r_in), ldf(X + L.glob_col * KP + j)));
+        const ff acc = ff_add(ff_add(ff_add(a0, a1), ff_add(a2, a3)), a4);
+        const float2 yo = Y[row * KP + j];
+        const ff yn = ff_norm(ff_add(ff_mul(cf, ff{yo.x, yo.y}), acc));
+        Y[row * KP + j] = make_float2(yn.h, yn.l);
+        if (Yk) Yk[(int64_t)pos * KP + j] = make_float2(yn.h, yn.l);
+        nrm = ff_add(nrm, ff_mul(yn, yn));
       }
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        a4 = ff_add(a4, ff_mul(rv(rec, 17 + k, r_in),
-                               ldf(X + (L.instr_base + rinstr(rec, k, r_in)) * KP + j)));
-      if (glob) a4 = ff_add(a4, ff_mul(rv(rec, 23, r_in), ldf(X + L.glob_col * KP + j)));
-      const ff acc = ff_add(ff_add(ff_add(a0, a1), ff_add(a2, a3)), a4);
-      const float2 yo = Y[row * KP + j];
-      const ff yn = ff_norm(ff_add(ff_mul(cf, ff{yo.x, yo.y}), acc));
-      Y[row * KP + j] = make_float2(yn.h, yn.l);
-      if (Yk) Yk[(int64_t)ri(rec, Rec<false>::POS, r_in) * KP + j] = make_float2(yn.h, yn.l);
-      nrm = ff_add(nrm, ff_mul(yn, yn));
     }
   }
   const double nv = ff_to_double(nrm);
@@ -289,73 +316,125 @@ __global__ void __launch_bounds__(256) k_aprod2_att_b(Layout L, const float2* __
 }
 
 // ---------------------------------------------------------------------------
-// aprod 2, k right-hand sides, instrumental part. Block b handles the
-// right-hand sides [c0, c0+kc) (c0 = (b / n_groups) * kc) for the tiles
-// ct = b % n_groups (mod n_groups). A histogram n_instr x kc of pairs and the
-// tile's Y slice live in shared memory; the rounds of distinct bins keep the
-// read-modify-writes conflict free. Entries are read from global memory; the
-// chunk groups walk the same tiles in the same order, so L2 serves repeats.
+// aprod 2, k right-hand sides, instrumental part. A histogram of all KP
+// right-hand sides per instrumental column does not fit one block's shared
+// memory, so the entries are regrouped instead: rows are cut into tiles of
+// 2^tile_log rows and the entries of every (tile, column) bucket are stored
+// contiguously (built once per system, InstrCsc). A stream of KP lanes owns a
+// bucket: it sums coef * Y[row][j] over the bucket in registers (no shared
+// memory, no barriers, no races) and adds the sum into X with one L2
+// reduction per lane. Buckets are taken tile-major so that the Y rows of the
+// tiles in flight stay in L2 while their 6 entries per row are gathered.
 // ---------------------------------------------------------------------------
-template <int KP>
-__global__ void __launch_bounds__(512, 1) k_aprod2_instr_b(Layout L, const float2* __restrict__ Y,
-                                                           double* __restrict__ X, int n_groups,
-                                                           int kc, const double* stop) {
-  if (stop && *stop != 0.0) return;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int CT = L.ct_rows;
-  float2* hist = reinterpret_cast<float2*>(smem);  // [n_instr][kc]
-  float2* ys = hist + L.n_instr * kc;             // [CT][kc]
-  const int group = blockIdx.x % n_groups;
-  const int c0 = (blockIdx.x / n_groups) * kc;
-  const int lkc = __ffs(kc) - 1;  // kc is a power of two
-  for (int i = threadIdx.x; i < L.n_instr * kc; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
-  for (int64_t ct = group; ct < L.n_ctiles; ct += n_groups) {
-    __syncthreads();
-    const int64_t r0 = ct * CT;
-    for (int i = threadIdx.x; i < CT * kc; i += blockDim.x) {
-      const int row = i >> lkc, jj = i & (kc - 1);
-      ys[i] = r0 + row < L.n_rows ? Y[(r0 + row) * KP + c0 + jj] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int64_t ea = L.round_entry[k], eb = L.round_entry[k + 1];
-      const int n_work = (int)(eb - ea) << lkc;
-      const uint32_t* keys = L.ient_key + ea;
-      const float2* vals = L.ient_ff + ea;
-      constexpr int U = 4;  // work items per thread per step, loads issued first
-      for (int wb = threadIdx.x; wb < n_work; wb += U * (int)blockDim.x) {
-        uint32_t key[U];
-        float2 vv[U];
+struct InstrCsc {
+  int tile_log = 0;
+  int64_t n_tiles = 0, n_bins = 0;
+  int64_t* off = nullptr;        // [n_tiles * n_bins + 1] first entry of each bucket
+  int32_t* row = nullptr;        // [6 n_rows] row of each entry
+  float2* val = nullptr;         // [6 n_rows] coefficient (pair)
+  unsigned int* cnt = nullptr;   // [n_tiles * n_bins] build scratch
+  int64_t cap_buckets = 0;
+};
+
+__global__ void k_csc_count(Layout L, int tile_log, int64_t n_bins, unsigned int* __restrict__ cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned char* rec = L.rec_ff + (r >> 6) * Rec<false>::BYTES;
+    const int64_t t = (r >> tile_log) * n_bins;
 #pragma unroll
-        for (int i = 0; i < U; ++i) {
-          const int w = wb + i * (int)blockDim.x;
-          const bool in = w < n_work;
-          const int e = in ? (w >> lkc) : 0;
-          key[i] = in ? __ldg(keys + e) : 0xffffffffu;
-          vv[i] = in ? __ldg(vals + e) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-          if (key[i] == 0xffffffffu) continue;
-          const int w = wb + i * (int)blockDim.x;
-          const int jj = w & (kc - 1);
-          const int row = (int)(key[i] >> INSTR_BIN_BITS);
-          const int bin = (int)(key[i] & ((1u << INSTR_BIN_BITS) - 1));
-          const float2 uu = ys[row * kc + jj];
-          const ff p = ff_mul(ff{vv[i].x, vv[i].y}, ff{uu.x, uu.y});
-          const float2 h = hist[bin * kc + jj];
-          const ff nh = ff_add(ff{h.x, h.y}, p);
-          hist[bin * kc + jj] = make_float2(nh.h, nh.l);
-        }
-      }
-      __syncthreads();
+    for (int k = 0; k < 6; ++k) atomicAdd(cnt + t + rinstr(rec, k, (int)(r & 63)), 1u);
+  }
+}
+
+// Exclusive prefix sum of n counts into off[0..n] (one block).
+__global__ void k_csc_scan(const unsigned int* __restrict__ cnt, int64_t n, int64_t* __restrict__ off) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t a0 = (int64_t)threadIdx.x * per;
+  const int64_t a = a0 < n ? a0 : n, b = a + per < n ? a + per : n;
+  int64_t sum = 0;
+  for (int64_t i = a; i < b; ++i) sum += cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (unsigned int t = 0; t < blockDim.x; ++t) {
+      const int64_t v = part[t];
+      part[t] = run;
+      run += v;
     }
+    off[n] = run;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < L.n_instr * kc; i += blockDim.x) {
-    const float2 h = hist[i];
-    red_ff_b(X + (L.instr_base + (i >> lkc)) * KP + c0 + (i & (kc - 1)), ff{h.x, h.y});
+  int64_t run = part[threadIdx.x];
+  for (int64_t i = a; i < b; ++i) {
+    off[i] = run;
+    run += cnt[i];
+  }
+}
+
+// Scatter the entries into their buckets (cnt reused as zeroed cursors; the
+// order inside a bucket follows the atomics).
+__global__ void k_csc_fill(Layout L, int tile_log, int64_t n_bins, const int64_t* __restrict__ off,
+                           unsigned int* __restrict__ cur, int32_t* __restrict__ row,
+                           float2* __restrict__ val) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned char* rec = L.rec_ff + (r >> 6) * Rec<false>::BYTES;
+    const int r_in = (int)(r & 63);
+    const int64_t t = (r >> tile_log) * n_bins;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int64_t bkt = t + rinstr(rec, k, r_in);
+      const int64_t pos = off[bkt] + atomicAdd(cur + bkt, 1u);
+      row[pos] = (int32_t)r;
+      const ff v = rv(rec, 17 + k, r_in);
+      val[pos] = make_float2(v.h, v.l);
+    }
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_aprod2_instr_csc(Layout L, const int64_t* __restrict__ off,
+                                                          const int32_t* __restrict__ erow,
+                                                          const float2* __restrict__ eval,
+                                                          int64_t n_buckets, int64_t n_bins,
+                                                          const float2* __restrict__ Y,
+                                                          double* __restrict__ X,
+                                                          const double* stop) {
+  if (stop && *stop != 0.0) return;
+  constexpr int S = 32 / KP;
+  const int lane = threadIdx.x & 31, q = lane / KP, j = lane % KP;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u0 = gw * S; u0 < n_buckets; u0 += nw * S) {
+    const int64_t u = u0 + q;
+    if (u >= n_buckets) continue;
+    const int64_t e0 = off[u], e1 = off[u + 1];
+    if (e0 == e1) continue;
+    ff acc = ff_zero();
+    constexpr int U = 4;  // entries per step, loads first
+    int64_t e = e0;
+    for (; e + U <= e1; e += U) {
+      int r[U];
+      float2 v[U], y[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        r[i] = __ldg(erow + e + i);
+        v[i] = __ldg(eval + e + i);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) y[i] = __ldg(Y + (int64_t)r[i] * KP + j);
+#pragma unroll
+      for (int i = 0; i < U; ++i)
+        acc = ff_add(acc, ff_mul(ff{v[i].x, v[i].y}, ff{y[i].x, y[i].y}));
+    }
+    for (; e < e1; ++e) {
+      const float2 v = __ldg(eval + e);
+      const float2 y = __ldg(Y + (int64_t)__ldg(erow + e) * KP + j);
+      acc = ff_add(acc, ff_mul(ff{v.x, v.y}, ff{y.x, y.y}));
+    }
+    red_ff_b(X + (L.instr_base + u % n_bins) * KP + j, acc);
   }
 }
 
@@ -661,13 +740,15 @@ struct BatchWork {
   double *sc = nullptr, *hsc = nullptr, *part = nullptr;
   unsigned int* count = nullptr;
   int threads = 256;  // block width of the row/knot kernels (tuned)
-  int kc = 1;         // right-hand sides per instrumental block (tuned)
+  InstrCsc csc;       // instrumental buckets; csc.tile_log is tuned
   bool tuned = false;
 };
 
 static void free_batch(BatchWork* w) {
   if (!w) return;
-  void* p[] = {w->U, w->Uk, w->Vff, w->V, w->W, w->XZ, w->Z, w->D, w->sc, w->part, w->count};
+  void* p[] = {w->U,    w->Uk,   w->Vff,        w->V,          w->W,          w->XZ,
+               w->Z,    w->D,    w->sc,         w->part,       w->count,      w->csc.off,
+               w->csc.row, w->csc.val, w->csc.cnt};
   for (void* q : p)
     if (q) cudaFree(q);
   if (w->hsc) cudaFreeHost(w->hsc);
@@ -685,7 +766,51 @@ static int kpad(int k) {
   return p;
 }
 
-static int batch_work(gsr_system* s, int KP, BatchWork** out) {
+// (Re)build the instrumental buckets for tiles of 2^tile_log rows.
+static int build_csc(gsr_system* s, BatchWork* w, int tile_log, cudaStream_t st) {
+  InstrCsc& C = w->csc;
+  const Layout& L = s->L;
+  const int64_t n_tiles = (L.n_rows + ((int64_t)1 << tile_log) - 1) >> tile_log;
+  const int64_t nb = n_tiles * L.n_instr;
+  cudaError_t e = cudaSuccess;
+  if (!C.row) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)&C.row, std::max<int64_t>(6 * L.n_rows, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&C.val, std::max<int64_t>(6 * L.n_rows, 1) * 8);
+  }
+  if (e == cudaSuccess && nb > C.cap_buckets) {
+    if (C.off) cudaFree(C.off);
+    if (C.cnt) cudaFree(C.cnt);
+    C.off = nullptr;
+    C.cnt = nullptr;
+    e = cudaMalloc((void**)&C.off, (nb + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&C.cnt, std::max<int64_t>(nb, 1) * 4);
+    C.cap_buckets = e == cudaSuccess ? nb : 0;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
+  }
+  C.tile_log = tile_log;
+  C.n_tiles = n_tiles;
+  C.n_bins = L.n_instr;
+  const int rb = (int)std::max<int64_t>(1, std::min<int64_t>((L.n_rows + 255) / 256,
+                                                             (int64_t)s->num_sms * 16));
+  if (cudaMemsetAsync(C.cnt, 0, nb * 4, st) != cudaSuccess) return GSR_E_CUDA;
+  k_csc_count<<<rb, 256, 0, st>>>(L, tile_log, L.n_instr, C.cnt);
+  k_csc_scan<<<1, 1024, 0, st>>>(C.cnt, nb, C.off);
+  if (cudaMemsetAsync(C.cnt, 0, nb * 4, st) != cudaSuccess) return GSR_E_CUDA;
+  k_csc_fill<<<rb, 256, 0, st>>>(L, tile_log, L.n_instr, C.off, C.cnt, C.row, C.val);
+  return cuda_status(cudaGetLastError());
+}
+
+// Tile height whose Y rows (KP pairs each) take about 32 MB of L2.
+static int default_tile_log(int KP) {
+  int lg = 12;
+  while (lg < 20 && ((int64_t)1 << (lg + 1)) * KP * 8 <= ((int64_t)32 << 20)) ++lg;
+  return lg;
+}
+
+static int batch_work(gsr_system* s, int KP, BatchWork** out, cudaStream_t st) {
   BatchWork* w = static_cast<BatchWork*>(s->batch);
   if (w && w->KP == KP) {
     *out = w;
@@ -722,14 +847,13 @@ static int batch_work(gsr_system* s, int KP, BatchWork** out) {
     return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
   }
   s->batch = w;
+  const int rc = build_csc(s, w, default_tile_log(KP), st);
+  if (rc != GSR_OK) {
+    destroy_batch(s);
+    return rc;
+  }
   *out = w;
   return GSR_OK;
-}
-
-static int instr_kc_max(const gsr_system* s, int KP) {
-  int kc = KP;
-  while (kc > 1 && (int64_t)(s->L.n_instr + s->L.ct_rows) * kc * 8 > INSTR_SMEM_BUDGET) kc >>= 1;
-  return kc;
 }
 
 template <int KP>
@@ -755,13 +879,13 @@ static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const 
   const int att_blocks = (L.n_att_warps + 7) / 8;
   if (att_blocks > 0) k_aprod2_att_b<KP><<<att_blocks, 256, 0, s->side>>>(L, Yk, X, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
-  const int kc = std::min(w->kc, instr_kc_max(s, KP));
-  const int chunks = KP / kc;
-  const int groups = std::max(1, (int)std::min<int64_t>(L.n_ctiles, s->num_sms / chunks > 0 ?
-                                                                      s->num_sms / chunks : 1));
-  const int ismem = (int)((L.n_instr + L.ct_rows) * kc * 8);
-  if (L.n_ctiles > 0)
-    k_aprod2_instr_b<KP><<<groups * chunks, 512, ismem, st>>>(L, Y, X, groups, kc, stop);
+  const InstrCsc& C = w->csc;
+  const int64_t nbk = C.n_tiles * C.n_bins;
+  if (nbk > 0) {
+    const int64_t warps = (nbk + (32 / KP) - 1) / (32 / KP);
+    const int ib = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)s->num_sms * 16);
+    k_aprod2_instr_csc<KP><<<ib, 256, 0, st>>>(L, C.off, C.row, C.val, nbk, C.n_bins, Y, X, stop);
+  }
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   const int wpb = w->threads / 32;
   const int ab = (int)std::min<int64_t>((L.n_recs + wpb - 1) / wpb, (int64_t)s->num_sms * 16);
@@ -792,63 +916,48 @@ static int aprod2_b(gsr_system* s, BatchWork* w, const float2* Y, const float2* 
   GSR_KP_DISPATCH(w->KP, (launch_aprod2_bt<KP>(s, w, Y, Yk, X, stop, st)));
 }
 
-static int set_batch_attributes() {
-  static bool done = false;
-  if (done) return GSR_OK;
-  cudaError_t e = cudaSuccess;
-#define GSR_SETATTR(KPV)                                                                     \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_aprod2_instr_b<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             INSTR_SMEM_BUDGET);
-  GSR_SETATTR(1) GSR_SETATTR(2) GSR_SETATTR(4) GSR_SETATTR(8) GSR_SETATTR(16) GSR_SETATTR(32)
-#undef GSR_SETATTR
-  if (e != cudaSuccess) return GSR_E_CUDA;
-  done = true;
-  return GSR_OK;
-}
-
 // The autotuner: times aprod 1 + aprod 2 for every (block width, instrumental
-// chunk) candidate on the system's own data and keeps the fastest.
+// tile height) candidate on the system's own data and keeps the fastest.
 static int autotune(gsr_system* s, BatchWork* w, cudaStream_t st) {
   if (w->tuned) return GSR_OK;
   const int widths[] = {128, 256};
-  std::vector<int> kcs;
-  for (int kc = instr_kc_max(s, w->KP); kc >= 1; kc >>= 1) kcs.push_back(kc);
+  const int d = default_tile_log(w->KP);
+  const int tiles[] = {d - 1, d, d + 1};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GSR_E_CUDA;
   float best = 1e30f;
-  int bw = 256, bkc = kcs.empty() ? 1 : kcs[0];
-  for (int width : widths) {
-    for (int kc : kcs) {
+  int bw = 256, bt = d;
+  int rc = GSR_OK;
+  for (int tl : tiles) {
+    if ((rc = build_csc(s, w, tl, st)) != GSR_OK) break;
+    for (int width : widths) {
       w->threads = width;
-      w->kc = kc;
       float t_min = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < 3 && rc == GSR_OK; ++rep) {
         cudaMemsetAsync(w->Z, 0, w->n_unk * w->KP * 8, st);
         cudaEventRecord(e0, st);
-        int rc = aprod1_b(s, w, w->Vff, w->U, nullptr, nullptr, nullptr, nullptr, st);
+        rc = aprod1_b(s, w, w->Vff, w->U, nullptr, nullptr, nullptr, nullptr, st);
         if (rc == GSR_OK) rc = aprod2_b(s, w, w->U, w->Uk, w->Z, nullptr, st);
         cudaEventRecord(e1, st);
-        if (rc != GSR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return GSR_E_CUDA;
-        }
+        if (rc == GSR_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = GSR_E_CUDA;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == GSR_OK) cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) t_min = std::min(t_min, ms);
       }
+      if (rc != GSR_OK) break;
       if (t_min < best) {
         best = t_min;
         bw = width;
-        bkc = kc;
+        bt = tl;
       }
     }
+    if (rc != GSR_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc != GSR_OK) return rc;
   w->threads = bw;
-  w->kc = bkc;
+  if (w->csc.tile_log != bt && (rc = build_csc(s, w, bt, st)) != GSR_OK) return rc;
   w->tuned = true;
   return GSR_OK;
 }
@@ -906,9 +1015,8 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
                gsr_lsqr_result* res, cudaStream_t st) {
   const int KP = kpad(k);
   BatchWork* w = nullptr;
-  int rc = batch_work(s, KP, &w);
+  int rc = batch_work(s, KP, &w, st);
   if (rc != GSR_OK) return rc;
-  if ((rc = set_batch_attributes()) != GSR_OK) return rc;
   const int64_t m = s->L.n_unk;
   const int64_t itnlim = o->itnlim > 0 ? o->itnlim : 20 * std::max<int64_t>(1, m);
   cudaError_t e = cudaSuccess;
@@ -1033,7 +1141,7 @@ int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* s
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int KP = gsr::kpad(k);
   gsr::BatchWork* w = nullptr;
-  int rc = gsr::batch_work(sys, KP, &w);
+  int rc = gsr::batch_work(sys, KP, &w, st);
   if (rc != GSR_OK) return rc;
   const int64_t m = sys->L.n_unk, n = sys->L.n_rows;
   const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
@@ -1053,9 +1161,8 @@ int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* s
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int KP = gsr::kpad(k);
   gsr::BatchWork* w = nullptr;
-  int rc = gsr::batch_work(sys, KP, &w);
+  int rc = gsr::batch_work(sys, KP, &w, st);
   if (rc != GSR_OK) return rc;
-  if ((rc = gsr::set_batch_attributes()) != GSR_OK) return rc;
   const int64_t m = sys->L.n_unk;
   const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
   const int bn = (int)std::min<int64_t>((sys->L.n_rows * KP + 255) / 256 + 1, sys->num_sms * 8);
@@ -1085,11 +1192,11 @@ int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
   return gsr::lsqr_batch(sys, k, B, X, opts, res, st);
 }
 
-int gsr_batch_tuning(const gsr_system* sys, int* threads, int* kc) {
+int gsr_batch_tuning(const gsr_system* sys, int* threads, int* tile_rows) {
   if (!sys || !sys->batch) return GSR_E_ARG;
   const gsr::BatchWork* w = static_cast<const gsr::BatchWork*>(sys->batch);
   if (threads) *threads = w->threads;
-  if (kc) *kc = w->kc;
+  if (tile_rows) *tile_rows = 1 << w->csc.tile_log;
   return GSR_OK;
 }
 

@@ -118,7 +118,7 @@ void free_system(gsr_system* s) {
                   s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
                   s->dscale, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
                   s->S.count, s->S.x_ff, s->S.x3,
-                  s->S.y_ff, s->S.y_knot};
+                  s->S.y_ff, s->S.y_knot, s->instr_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->host_scal) cudaFreeHost(s->host_scal);

@@ -269,6 +269,7 @@ struct gsr_system {
   double* scal;          // device LSQR scalars
   double* host_scal;     // pinned mirror of scal
   void* batch;           // multi-right-hand-side workspace (allocated on first use)
+  int* instr_count;      // [n_instr] rows per instrumental column (learned features)
   cudaStream_t side;     // second stream for the attitude part of aprod 2
   cudaEvent_t ev_fork, ev_join;
   int main_block, main_ctas, main_smem;

@@ -93,6 +93,18 @@ def _load():
     lib.gsr_batch_tuning.argtypes = [_c_p, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int)]
     lib.gsr_batch_tuning.restype = ctypes.c_int
+    lib.gsr_n_learned_cols.argtypes = [_c_p]
+    lib.gsr_n_learned_cols.restype = _c_i64
+    lib.gsr_column_features.argtypes = [_c_p, _c_p, _c_p]
+    lib.gsr_feature_moments.argtypes = [_c_p, _c_i64, _c_p, _c_p]
+    lib.gsr_mlp_forward.argtypes = [_c_p, _c_i64, _c_p, _c_p, _c_p, _c_p]
+    lib.gsr_mlp_grad.argtypes = [_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]
+    lib.gsr_mlp_adam.argtypes = [_c_p, _c_p, _c_p, _c_p, _c_i64, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, _c_p]
+    lib.gsr_learned_scaling.argtypes = [_c_p, _c_p, ctypes.c_float, _c_p, _c_p]
+    for name in ("gsr_column_features", "gsr_feature_moments", "gsr_mlp_forward", "gsr_mlp_grad",
+                 "gsr_mlp_adam", "gsr_learned_scaling"):
+        getattr(lib, name).restype = ctypes.c_int
     return lib
 
 
@@ -142,6 +154,8 @@ class System:
         self._h = h
         self.n_rows = int(lib.gsr_n_rows(h))
         self.n_unk = int(lib.gsr_n_unknowns(h))
+        self.n_stars, self.n_knots = int(sys["n_stars"]), int(sys["n_knots"])
+        self.n_instr, self.n_glob = int(sys["n_instr"]), int(sys["n_glob"])
         self.storage = storage
 
     def close(self):
@@ -290,7 +304,7 @@ def _batch_methods():
     def batch_tuning(self):
         t, c = ctypes.c_int(), ctypes.c_int()
         _check(lib.gsr_batch_tuning(self._h, ctypes.byref(t), ctypes.byref(c)), "gsr_batch_tuning")
-        return dict(threads=t.value, kc=c.value)
+        return dict(threads=t.value, tile_rows=c.value)
 
     System.aprod1_batch = aprod1_batch
     System.aprod2_batch = aprod2_batch
@@ -299,3 +313,82 @@ def _batch_methods():
 
 
 _batch_methods()
+
+
+# ---------------------------------------------------------------------------
+# Learned column preconditioner: the MLP kernels (current device, current
+# stream). Tensors are float32 CUDA tensors; theta has MLP_NPARAM entries.
+# ---------------------------------------------------------------------------
+MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM, MLP_GRID = 8, 64, 4801, 296
+MLP_WORK_FLOATS = MLP_GRID * (MLP_NPARAM + 1)
+
+
+def _fptr(t, n, name):
+    return _dptr(t, n, name, dtype=torch.float32)
+
+
+def feature_moments(feats, acc):
+    """acc[16] (float64) += column sums of feats and of feats**2."""
+    n = int(feats.shape[0])
+    _check(lib.gsr_feature_moments(_fptr(feats, n * MLP_NFEAT, "feats"), n,
+                                   _dptr(acc, 2 * MLP_NFEAT, "acc"), _stream()),
+           "gsr_feature_moments")
+    return acc
+
+
+def mlp_forward(feats, norm, theta, out=None):
+    """Network outputs m[n] for raw features feats[n, 8]."""
+    n = int(feats.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feats.device)
+    _check(lib.gsr_mlp_forward(_fptr(feats, n * MLP_NFEAT, "feats"), n,
+                               _fptr(norm, 2 * MLP_NFEAT, "norm"), _fptr(theta, MLP_NPARAM, "theta"),
+                               _fptr(out, n, "out"), _stream()), "gsr_mlp_forward")
+    return out
+
+
+def mlp_grad(feats, target, norm, theta, work, grad, loss=None):
+    """grad = dL/dtheta of the mean squared error; loss[1] = L if given."""
+    n = int(feats.shape[0])
+    _check(lib.gsr_mlp_grad(_fptr(feats, n * MLP_NFEAT, "feats"), _fptr(target, n, "target"), n,
+                            _fptr(norm, 2 * MLP_NFEAT, "norm"), _fptr(theta, MLP_NPARAM, "theta"),
+                            _fptr(work, MLP_WORK_FLOATS, "work"), _fptr(grad, MLP_NPARAM, "grad"),
+                            _fptr(loss, 1, "loss") if loss is not None else None, _stream()),
+           "gsr_mlp_grad")
+    return grad
+
+
+def mlp_adam(theta, grad, mom, vel, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step on theta (in place)."""
+    _check(lib.gsr_mlp_adam(_fptr(theta, MLP_NPARAM, "theta"), _fptr(grad, MLP_NPARAM, "grad"),
+                            _fptr(mom, MLP_NPARAM, "mom"), _fptr(vel, MLP_NPARAM, "vel"), int(step),
+                            lr, beta1, beta2, eps, _stream()), "gsr_mlp_adam")
+    return theta
+
+
+def _learned_methods():
+    def n_learned_cols(self):
+        return int(lib.gsr_n_learned_cols(self._h))
+
+    def column_features(self):
+        """Features [3K + n_instr, 8] (float32) of the attitude + instrumental columns."""
+        nq = self.n_learned_cols()
+        f = torch.empty((nq, MLP_NFEAT), dtype=torch.float32, device=self.device)
+        _check(lib.gsr_column_features(self._h, _fptr(f, nq * MLP_NFEAT, "feats"), _stream()),
+               "gsr_column_features")
+        return f
+
+    def learned_scaling(self, m=None, clamp=3.0):
+        """Column scaling d [N_unk] (float64): exp(m_q) / ||A_:,j|| on the learned columns."""
+        d = torch.empty(self.n_unk, dtype=torch.float64, device=self.device)
+        mp = _fptr(m, self.n_learned_cols(), "m") if m is not None else None
+        _check(lib.gsr_learned_scaling(self._h, mp, float(clamp), _c_p(d.data_ptr()), _stream()),
+               "gsr_learned_scaling")
+        return d
+
+    System.n_learned_cols = n_learned_cols
+    System.column_features = column_features
+    System.learned_scaling = learned_scaling
+
+
+_learned_methods()

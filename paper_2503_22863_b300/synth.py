@@ -146,3 +146,14 @@ def learned_system_params(s):
     return dict(n_stars=200_000, obs=30, poisson=True, n_knots=k, n_instr=ni, n_glob=1,
                 seed=25030400 + s)
 
+
+
+def mlp_init_params(seed):
+    """Initial parameters of the learned-preconditioner MLP (8 -> 64 -> 64 -> 1),
+    flat float64 in the order W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3:
+    normal weights with standard deviations sqrt(2/8), sqrt(2/64), sqrt(1/64)
+    (He initialisation) and zero biases, from a seeded PCG64 stream."""
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    return np.concatenate([g.normal(0.0, math.sqrt(2.0 / 8), 64 * 8), np.zeros(64),
+                           g.normal(0.0, math.sqrt(2.0 / 64), 64 * 64), np.zeros(64),
+                           g.normal(0.0, math.sqrt(1.0 / 64), 64), np.zeros(1)])

@@ -47,6 +47,32 @@ def test_batched_aprod_parity(gsr, k):
         assert scaled_err(Xg[:, j], ref2, scale2) <= APROD_TOL, ("aprod2", j)
 
 
+@pytest.mark.parametrize("k,n_stars", [(32, 10000), (5, 20000)])
+def test_batched_aprod_multi_tile(gsr, k, n_stars):
+    # more rows than one instrumental row tile (2^17 rows at k = 32, 2^19 at
+    # k <= 8), with a ragged last tile
+    sys = synth.make_system(n_stars=n_stars, n_knots=2000, n_instr=700, n_glob=1, obs=30,
+                            seed=91 + k)
+    rng = np.random.default_rng(100 + k)
+    with gsr.System(sys) as S:
+        assert S.n_rows > (1 << 17 if k > 8 else 1 << 19)
+        X = rng.standard_normal((S.n_unk, k))
+        Y0 = rng.standard_normal((S.n_rows, k))
+        Y = to_dev(Y0)
+        S.aprod1_batch(to_dev(X), Y)
+        Yg = to_host(Y)
+        U = rng.standard_normal((S.n_rows, k))
+        X0 = rng.standard_normal((S.n_unk, k))
+        Xo = to_dev(X0)
+        S.aprod2_batch(to_dev(U), Xo)
+        Xg = to_host(Xo)
+    for j in (0, k // 2, k - 1):
+        ref, scale = aprod1_ref(sys, X[:, j], Y0[:, j])
+        assert scaled_err(Yg[:, j], ref, scale) <= APROD_TOL, ("aprod1", j)
+        ref2, scale2 = aprod2_ref(sys, U[:, j], X0[:, j])
+        assert scaled_err(Xg[:, j], ref2, scale2) <= APROD_TOL, ("aprod2", j)
+
+
 @pytest.fixture(scope="module")
 def tiny_batch():
     sys = synth.make_system(n_rhs=5, **synth.CONFIGS["tiny"])
@@ -63,7 +89,8 @@ def test_batched_lsqr_matches_oracle_and_single(gsr, tiny_batch):
         r = S.lsqr_batch(to_dev(B), atol=1e-14, btol=1e-14)
         X = to_host(r["x"])
         tun = S.batch_tuning()
-        assert tun["threads"] in (128, 256) and tun["kc"] >= 1
+        assert tun["threads"] in (128, 256)
+        assert tun["tile_rows"] >= 1 and tun["tile_rows"] & (tun["tile_rows"] - 1) == 0
         for j in (0, k - 1):
             single = S.lsqr(to_dev(B[:, j]), atol=1e-14, btol=1e-14)
             assert relerr(X[:, j], to_host(single["x"])) <= LSQR_TOL
