@@ -69,18 +69,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+def profiled_traffic(kernel, n_rows):
+    """DRAM bytes per launch (read + write) from the committed ncu summary of the
+    kernel group on the small workload, scaled to n_rows (the traffic of these
+    row-streaming kernels grows with the rows processed), if that summary was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "%s_small.md" % kernel)
     if not os.path.exists(p):
         return None
     text = open(p).read()
     m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(r"dram_bytes_per_row:\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
-    return float(t.group(1))
+    return float(t.group(1)) * n_rows
 
 
 class ClockSampler:
@@ -479,11 +481,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, sys_), "n_rows": n_rows,
                    "n_unk": n_unk, "iterations_to_1e9": n_star, "final_rel_err": err,
-                   "l2": "inputs larger than L2 (matrix ~10 GB resident in HBM)",
+                   "l2": "inputs larger than L2 (system ~11.5 GB resident in HBM)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
-                     "traffic": profiled_traffic(dom, args.workload)},
+                     "traffic": profiled_traffic(dom, n_rows)},
         "aprod": {"aprod1_ms": t_a1, "aprod1_GBps": gbs1, "aprod2_ms": t_a2, "aprod2_GBps": gbs2,
                   "vector_ms": t_vec, "iterations_per_s": 1e3 / (t_a1 + t_a2 + t_vec),
                   "bytes_per_launch": {"aprod1": by1, "aprod2": by2}},

@@ -19,7 +19,7 @@
 //   att         start-knot-ordered copy, sliding 4-knot window per axis.
 #include <algorithm>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace gsr {
 
@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
 }
 
 // ---------------------------------------------------------------------------
-// aprod 2, astrometric + global part. One warp per record (grid-stride), the
-// two rows of a lane are consecutive; per-star runs are summed in registers,
-// joined across lanes by a segmented inclusive scan and added into x once per
-// record (a star whose rows span records gets one add per record).
+// aprod 2, astrometric + global part. One warp per two records (grid-stride),
+// the four rows of a lane are consecutive; per-star runs are summed in
+// registers, joined across lanes by a segmented inclusive scan and added into
+// x once per record pair (a star whose rows span pairs gets one add per pair).
 // ---------------------------------------------------------------------------
 struct Astro {
   ff c[5];
@@ -385,47 +385,94 @@ __global__ void __launch_bounds__(256) k_aprod2_astro(Layout L, const float2* __
                                                       double* __restrict__ x, const double* stop) {
   if (stop && *stop != 0.0) return;
   using R = Rec<F32>;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, lp = lane & 15;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
   const bool glob = L.n_glob == 1;
+  const int64_t n_pairs = (L.n_recs + 1) / 2;
   ff gacc = ff_zero();
-  for (int64_t r = gw; r < L.n_recs; r += nw) {
-    const unsigned char* rec = recs + r * R::BYTES;
-    const int64_t row0 = r * REC_ROWS + 2 * lane;
-    // y is padded to whole records (zeros), so the pair load is in bounds
-    const float4 ya = __ldcs(reinterpret_cast<const float4*>(y + row0));
-    const int2 st = __ldcs(reinterpret_cast<const int2*>(rec + R::STAR + lane * 8));
-    ff v[6][2];
+  // A warp takes two consecutive records (128 rows); lane l holds rows
+  // 4(l%16) .. 4(l%16)+3 of record 2p + l/16, so one cross-lane scan serves
+  // 128 rows. Runs are merged inside the lane first.
+  for (int64_t pr = gw; pr < n_pairs; pr += nw) {
+    const int64_t rl = 2 * pr + (lane >> 4);
+    const bool have = rl < L.n_recs;
+    const unsigned char* rec = recs + (have ? rl : 2 * pr) * R::BYTES;
+    int s[4];
+    ff v[6][4];
+    float4 ya = make_float4(0.f, 0.f, 0.f, 0.f), yb = ya;
+    if (have) {
+      // y is padded to whole records (zeros), so these loads are in bounds
+      const float4* yp = reinterpret_cast<const float4*>(y + rl * REC_ROWS + 4 * lp);
+      ya = __ldcs(yp);
+      yb = __ldcs(yp + 1);
+      const int4 st = __ldcs(reinterpret_cast<const int4*>(rec + R::STAR + lp * 16));
+      s[0] = st.x;
+      s[1] = st.y;
+      s[2] = st.z;
+      s[3] = st.w;
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      const int slot = t < 5 ? t : 23;
-      if constexpr (F32) {
-        const float2 a =
-            __ldcs(reinterpret_cast<const float2*>(rec + slot_offset<true>(slot) + lane * 8));
-        v[t][0] = ff{a.x, 0.0f};
-        v[t][1] = ff{a.y, 0.0f};
+      for (int t = 0; t < 6; ++t) {
+        const int slot = t < 5 ? t : 23;
+        if constexpr (F32) {
+          const float4 a =
+              __ldcs(reinterpret_cast<const float4*>(rec + slot_offset<true>(slot) + lp * 16));
+          v[t][0] = ff{a.x, 0.0f};
+          v[t][1] = ff{a.y, 0.0f};
+          v[t][2] = ff{a.z, 0.0f};
+          v[t][3] = ff{a.w, 0.0f};
+        } else {
+          const float4* q =
+              reinterpret_cast<const float4*>(rec + slot_offset<false>(slot) + lp * 32);
+          const float4 a = __ldcs(q), c = __ldcs(q + 1);
+          v[t][0] = ff{a.x, a.y};
+          v[t][1] = ff{a.z, a.w};
+          v[t][2] = ff{c.x, c.y};
+          v[t][3] = ff{c.z, c.w};
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[t][k] = ff_zero();
+    }
+    // a lane without a record continues the last star of lane 15 with zeros
+    const int s_last15 = __shfl_sync(0xffffffffu, have ? s[3] : 0, 15);
+    if (!have) s[0] = s[1] = s[2] = s[3] = s_last15;
+    const ff u[4] = {ff{ya.x, ya.y}, ff{ya.z, ya.w}, ff{yb.x, yb.y}, ff{yb.z, yb.w}};
+    Astro pk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int t = 0; t < 5; ++t) pk[k].c[t] = val_mul<F32>(v[t][k], u[k]);
+    if (glob)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gacc = ff_add(gacc, val_mul<F32>(v[5][k], u[k]));
+
+    // in-lane runs: head = run of s[0], tail = run of s[3]; a run strictly
+    // between them is complete here and is flushed at once
+    Astro acc = pk[0], head = pk[0];
+    bool head_done = false;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      if (s[k] == s[k - 1]) {
+        acc = astro_add(acc, pk[k]);
       } else {
-        const float4 a =
-            __ldcs(reinterpret_cast<const float4*>(rec + slot_offset<false>(slot) + lane * 16));
-        v[t][0] = ff{a.x, a.y};
-        v[t][1] = ff{a.z, a.w};
+        if (!head_done) {
+          head = acc;
+          head_done = true;
+        } else {
+          astro_flush(x, s[k - 1], acc);
+        }
+        acc = pk[k];
       }
     }
-    const ff uf0 = ff{ya.x, ya.y}, uf1 = ff{ya.z, ya.w};
-    Astro p0, p1;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      p0.c[t] = val_mul<F32>(v[t][0], uf0);
-      p1.c[t] = val_mul<F32>(v[t][1], uf1);
-    }
-    if (glob) gacc = ff_add(gacc, ff_add(val_mul<F32>(v[5][0], uf0), val_mul<F32>(v[5][1], uf1)));
-
-    const int s0 = st.x, s1 = st.y;
+    const int s0 = s[0], s1 = s[3];
     const bool uniform = (s0 == s1);
-    const Astro head = uniform ? astro_add(p0, p1) : p0;
-    const Astro tail = uniform ? head : p1;
+    if (uniform) head = acc;
+    const Astro tail = acc;
     // segmented inclusive scan of the tail runs across lanes
     const int prev_last = __shfl_up_sync(0xffffffffu, s1, 1);
     int flag = (lane == 0) || !uniform || (s0 != prev_last);
@@ -440,7 +487,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro(Layout L, const float2* __
       }
     }
     const Astro vprev = astro_shfl_up(V, 1);
-    if (!uniform) {  // the run of row 0 ends inside this lane
+    if (!uniform) {  // the run of the lane's first row ends inside this lane
       Astro tot = head;
       if (lane > 0 && s0 == prev_last) tot = astro_add(tot, vprev);
       astro_flush(x, s0, tot);
@@ -458,55 +505,71 @@ __global__ void __launch_bounds__(256) k_aprod2_astro(Layout L, const float2* __
 // aprod 2, instrumental part. One block per tile of ct_rows rows (grid-stride).
 // The tile's entries (coefficient, row, bin) are sorted at setup into rounds
 // in which every bin appears at most once; they are TMA-copied into shared
-// memory together with the tile's u, and each round adds its products into
-// the block's float-pair histogram with plain read-modify-write (distinct
-// bins: no conflicts), a barrier separating rounds. The histogram is added
-// into x at the end.
+// memory together with the tile's u (two buffers: the block's next tile
+// streams in while it works on the current one), and each round adds its
+// products into the block's float-pair histogram with plain read-modify-write
+// (distinct bins: no conflicts), a barrier separating rounds. The histogram
+// is added into x at the end.
 // ---------------------------------------------------------------------------
-template <bool F32>
-__global__ void __launch_bounds__(512, 1)
+template <bool F32, int NBUF, int NTH>
+__global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     k_aprod2_instr(Layout L, const float2* __restrict__ y, double* __restrict__ x,
                    const double* stop) {
   if (stop && *stop != 0.0) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   constexpr int VB = F32 ? 4 : 8;  // bytes per entry coefficient
   const int CT = L.ct_rows;
-  // [keys 6*CT u32 | coefficients 6*CT | u pairs CT | histogram n_instr pairs]
-  uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
-  unsigned char* vals = smem + 6 * CT * 4;
-  float2* us = reinterpret_cast<float2*>(vals + 6 * CT * VB);
-  float2* hist = us + CT;
+  const int64_t TB = instr_tile_bytes(CT, F32);
+  // [buffer 0 | buffer 1 | histogram n_instr pairs], a buffer being
+  // [keys 6*CT u32 | coefficients 6*CT | u pairs CT]
+  float2* hist = reinterpret_cast<float2*>(smem + NBUF * TB);
   for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_proxy_async();
   }
   __syncthreads();
-  uint32_t parity = 0;
-  bool ok = true;
-  for (int64_t ct = blockIdx.x; ct < L.n_ctiles; ct += gridDim.x) {
-    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
-    const int64_t e0 = L.round_entry[k0], e1 = L.round_entry[k1];
+  // thread 0: start the copies of tile ct into buffer b
+  auto issue = [&](int64_t ct, int b) {
+    unsigned char* base = smem + b * TB;
+    const int64_t e0 = L.round_entry[L.ct_round[ct]], e1 = L.round_entry[L.ct_round[ct + 1]];
     const int64_t ne = e1 - e0;
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      // sizes rounded up to 16 bytes (the entry arrays are padded for this);
-      // u is padded to whole tiles, so the full tile is always in bounds
-      const uint32_t kb = (uint32_t)((ne * 4 + 15) & ~15LL);
-      const uint32_t vb = (uint32_t)((ne * VB + 15) & ~15LL);
-      const uint32_t ub = (uint32_t)CT * 8u;
-      mbar_expect_tx(&bar, kb + vb + ub);
-      tma_load(us, y + ct * CT, ub, &bar);
-      if (ne > 0) {
-        tma_load(keys, L.ient_key + e0, kb, &bar);
-        if constexpr (F32) tma_load(vals, L.ient_f32 + e0, vb, &bar);
-        else tma_load(vals, L.ient_ff + e0, vb, &bar);
-      }
+    fence_proxy_async();
+    // sizes rounded up to 16 bytes (the entry arrays are padded for this);
+    // u is padded to whole tiles, so the full tile is always in bounds
+    const uint32_t kb = (uint32_t)((ne * 4 + 15) & ~15LL);
+    const uint32_t vb = (uint32_t)((ne * VB + 15) & ~15LL);
+    const uint32_t ub = (uint32_t)CT * 8u;
+    mbar_expect_tx(&bar[b], kb + vb + ub);
+    tma_load(base + 6 * CT * 4 + 6 * CT * VB, y + ct * CT, ub, &bar[b]);
+    if (ne > 0) {
+      tma_load(base, L.ient_key + e0, kb, &bar[b]);
+      if constexpr (F32) tma_load(base + 6 * CT * 4, L.ient_f32 + e0, vb, &bar[b]);
+      else tma_load(base + 6 * CT * 4, L.ient_ff + e0, vb, &bar[b]);
+    }
+  };
+  uint32_t parity = 0u, pending = 0u;  // bit q: phase / copy in flight of buffer q
+  bool ok = true;
+  int b = 0;
+  if (NBUF == 2 && blockIdx.x < L.n_ctiles) {
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    pending = 1u;
+  }
+  for (int64_t ct = blockIdx.x; ct < L.n_ctiles; ct += gridDim.x, b ^= (NBUF - 1)) {
+    // the buffer written here was last read by the previous tile, which ended
+    // in a barrier
+    if (NBUF == 1) {
+      if (threadIdx.x == 0) issue(ct, 0);
+      pending = 1u;
+    } else if (ct + gridDim.x < L.n_ctiles) {
+      if (threadIdx.x == 0) issue(ct + gridDim.x, b ^ 1);
+      pending |= 1u << (b ^ 1);
     }
     bool got = false;
     for (int i = 0; i < WAIT_LIMIT; ++i)
-      if (mbar_try_wait(&bar, parity)) {
+      if (mbar_try_wait(&bar[b], (parity >> b) & 1u)) {
         got = true;
         break;
       }
@@ -515,10 +578,16 @@ __global__ void __launch_bounds__(512, 1)
       ok = false;
       break;
     }
-    parity ^= 1u;
+    parity ^= 1u << b;
+    pending &= ~(1u << b);
+    const uint32_t* keys = reinterpret_cast<const uint32_t*>(smem + b * TB);
+    const unsigned char* vals = smem + b * TB + 6 * CT * 4;
+    const float2* us = reinterpret_cast<const float2*>(vals + 6 * CT * VB);
+    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
+    const int64_t e0 = L.round_entry[k0];
     for (int k = k0; k < k1; ++k) {
-      const int a = (int)(L.round_entry[k] - e0), b = (int)(L.round_entry[k + 1] - e0);
-      for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+      const int a = (int)(L.round_entry[k] - e0), bb = (int)(L.round_entry[k + 1] - e0);
+      for (int e = a + threadIdx.x; e < bb; e += blockDim.x) {
         const uint32_t key = keys[e];
         const int row = (int)(key >> INSTR_BIN_BITS);
         const int bin = (int)(key & ((1u << INSTR_BIN_BITS) - 1));
@@ -538,8 +607,11 @@ __global__ void __launch_bounds__(512, 1)
     }
   }
   if (!ok) {
-    for (int i = 0; i < WAIT_LIMIT / 16; ++i)
-      if (mbar_try_wait(&bar, parity)) break;
+    // let the copies still in flight land before the block exits (bounded)
+    for (int q = 0; q < NBUF; ++q)
+      if ((pending >> q) & 1u)
+        for (int i = 0; i < WAIT_LIMIT / 16; ++i)
+          if (mbar_try_wait(&bar[q], (parity >> q) & 1u)) break;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) {
@@ -551,9 +623,10 @@ __global__ void __launch_bounds__(512, 1)
 // ---------------------------------------------------------------------------
 // aprod 2, attitude part over the knot-sorted copy: a warp walks its range of
 // start knots; positions with start knot s add into knots s..s+3 of each
-// axis. A sliding 4-knot window per axis lives in registers; knot s is final
-// (for this warp) once bucket s is done and is added into x. Every load of a
-// step (U positions per lane) is issued before any arithmetic.
+// axis. A sliding 4-knot window per axis of per-lane partial sums lives in
+// registers; knot s is final (for this warp) once bucket s is done, and is
+// then summed over the warp and added into x. Every load of a step (U
+// positions per lane) is issued before any arithmetic.
 // ---------------------------------------------------------------------------
 template <bool F32>
 __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
@@ -606,16 +679,17 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
         acc[t] = ff_add(acc[t], sum);
       }
     }
-#pragma unroll
-    for (int t = 0; t < 12; ++t) acc[t] = ff_warp_sum(acc[t]);
+    // the windows hold this lane's partial sums; only a finished knot is
+    // reduced over the warp (3 values instead of 12 per bucket)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < 4; ++j) win[a][j] = ff_add(win[a][j], acc[4 * a + j]);
-    // knot s is complete for this warp
-    if (lane < 3) {
-      const ff w0 = lane == 0 ? win[0][0] : lane == 1 ? win[1][0] : win[2][0];
-      red_ff(x + L.att_base + lane * K + s, w0);
+    {
+      // knot s is complete for this warp
+      const ff k0 = ff_warp_sum(win[0][0]), k1 = ff_warp_sum(win[1][0]),
+               k2 = ff_warp_sum(win[2][0]);
+      if (lane < 3) red_ff(x + L.att_base + lane * K + s, lane == 0 ? k0 : lane == 1 ? k1 : k2);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -626,12 +700,11 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
     }
   }
   // the three knots after the last bucket also received contributions
-  if (lane < 3) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const ff wj = lane == 0 ? win[0][j] : lane == 1 ? win[1][j] : win[2][j];
-      red_ff(x + L.att_base + lane * K + s_end + j, wj);
-    }
+  for (int j = 0; j < 3; ++j) {
+    const ff k0 = ff_warp_sum(win[0][j]), k1 = ff_warp_sum(win[1][j]), k2 = ff_warp_sum(win[2][j]);
+    if (lane < 3)
+      red_ff(x + L.att_base + lane * K + s_end + j, lane == 0 ? k0 : lane == 1 ? k1 : k2);
   }
 }
 
@@ -663,10 +736,12 @@ int set_kernel_attributes() {
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
   C(cudaFuncSetAttribute(k_aprod1<true, false, false, A1_NW, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod2_instr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+#define GSR_INSTR_ATTR(F, B, T)                                                             \
+  C(cudaFuncSetAttribute(k_aprod2_instr<F, B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          INSTR_SMEM_BUDGET));
-  C(cudaFuncSetAttribute(k_aprod2_instr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         INSTR_SMEM_BUDGET));
+  GSR_INSTR_ATTR(false, 1, 256) GSR_INSTR_ATTR(true, 1, 256)
+  GSR_INSTR_ATTR(false, 2, 512) GSR_INSTR_ATTR(true, 2, 512)
+#undef GSR_INSTR_ATTR
   return cuda_status(e);
 }
 
@@ -773,14 +848,19 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
     else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
-  const int ib = (int)std::min<int64_t>(sys->num_sms, L.n_ctiles);
-  const int ismem = (int)instr_smem_bytes(L.ct_rows, L.n_instr, f32);
+  const int ib = (int)std::min<int64_t>((int64_t)sys->num_sms * L.ct_per_sm, L.n_ctiles);
+  const int ismem = (int)instr_smem_bytes(L.ct_rows, L.n_instr, f32, L.ct_bufs);
   if (ib > 0) {
-    if (f32) k_aprod2_instr<true><<<ib, 512, ismem, st>>>(L, y, x, stop);
-    else k_aprod2_instr<false><<<ib, 512, ismem, st>>>(L, y, x, stop);
+    if (L.ct_per_sm == 1) {
+      if (f32) k_aprod2_instr<true, 2, 512><<<ib, 512, ismem, st>>>(L, y, x, stop);
+      else k_aprod2_instr<false, 2, 512><<<ib, 512, ismem, st>>>(L, y, x, stop);
+    } else {
+      if (f32) k_aprod2_instr<true, 1, 256><<<ib, 256, ismem, st>>>(L, y, x, stop);
+      else k_aprod2_instr<false, 1, 256><<<ib, 256, ismem, st>>>(L, y, x, stop);
+    }
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
-  const int ab = (int)std::min<int64_t>((int64_t)sys->num_sms * 8, (L.n_recs + 7) / 8);
+  const int ab = (int)std::min<int64_t>((int64_t)sys->num_sms * 8, ((L.n_recs + 1) / 2 + 7) / 8);
   if (f32) k_aprod2_astro<true><<<ab, 256, 0, st>>>(L, y, x, stop);
   else k_aprod2_astro<false><<<ab, 256, 0, st>>>(L, y, x, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;

@@ -17,7 +17,7 @@
 #include <cstring>
 #include <vector>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace gsr {
 
@@ -245,15 +245,23 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
 // range; within a bucket the streams split the positions, then sums are joined
 // across streams and the 4-knot window per axis advances as in the single form.
 // ---------------------------------------------------------------------------
+constexpr int ATT_B_SPLIT = 2;  // warps per knot range of the single-vector partition
+
 template <int KP>
-__global__ void __launch_bounds__(256) k_aprod2_att_b(Layout L, const float2* __restrict__ Yk,
-                                                      double* __restrict__ X, const double* stop) {
+__global__ void __launch_bounds__(256, 2) k_aprod2_att_b(Layout L, const float2* __restrict__ Yk,
+                                                         double* __restrict__ X,
+                                                         const double* stop) {
   if (stop && *stop != 0.0) return;
   constexpr int S = 32 / KP;
   const int lane = threadIdx.x & 31, q = lane / KP, j = lane % KP;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  // ATT_B_SPLIT warps share each knot range of the single-vector partition
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = gw / ATT_B_SPLIT;
+  const int part = (int)(gw % ATT_B_SPLIT);
   if (gwarp >= L.n_att_warps) return;
-  const int s_begin = L.att_warp_knot[gwarp], s_end = L.att_warp_knot[gwarp + 1];
+  const int r0 = L.att_warp_knot[gwarp], r1 = L.att_warp_knot[gwarp + 1];
+  const int s_begin = r0 + (int)(((int64_t)(r1 - r0) * part) / ATT_B_SPLIT);
+  const int s_end = r0 + (int)(((int64_t)(r1 - r0) * (part + 1)) / ATT_B_SPLIT);
   if (s_begin >= s_end) return;
   const int64_t K = L.n_knots;
   ff win[3][4];
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(256) k_aprod2_att_b(Layout L, const float2* __
     ff acc[12];
 #pragma unroll
     for (int t = 0; t < 12; ++t) acc[t] = ff_zero();
-    constexpr int U = 4;  // positions per stream per step, all loads issued first
+    constexpr int U = 2;  // positions per stream per step, all loads issued first
     for (int64_t pb = p0 + q; pb < p1; pb += U * S) {
       ff u[U];
       float2 v[12][U];
@@ -530,27 +538,33 @@ __global__ void __launch_bounds__(256) k_xref2_b(int64_t n, const double* __rest
 }
 
 template <int KP>
-__global__ void __launch_bounds__(256) k_vec_a_b(int64_t n, const double* __restrict__ d,
+__global__ void __launch_bounds__(256) k_vec_a_b(int64_t n, const float2* __restrict__ d,
                                                  const double* __restrict__ Z,
-                                                 double* __restrict__ V, double* sc, double* part,
+                                                 float2* __restrict__ V, double* sc, double* part,
                                                  unsigned int* counter, int first) {
   __shared__ double tot[32];
   const double* g = sc + B_COUNT * KP;
   if (g[G_ALLDONE] != 0.0) return;
   const int j = threadIdx.x % KP;
   const double beta = sqrt(sc[B_UNORM2 * KP + j]);
-  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  const ff ib = ff_from_double(beta > 0.0 ? 1.0 / beta : 0.0), nbeta = ff_from_double(-beta);
   const bool frozen = sc[B_DONE * KP + j] != 0.0;
-  double s2 = 0.0;
+  ff s2f = ff_zero();
   if (!frozen) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
          e += (int64_t)gridDim.x * blockDim.x) {
-      double t = d[e / KP] * Z[e] * ib;
-      if (!first) t = __fma_rn(-beta, V[e], t);
-      V[e] = t;
-      s2 = __fma_rn(t, t, s2);
+      const float2 dj = d[e / KP];
+      ff t = ff_mul(ff_norm(ff_mul(ff{dj.x, dj.y}, ff_from_double(Z[e]))), ib);
+      if (!first) {
+        const float2 ve = V[e];
+        t = ff_add(t, ff_mul(nbeta, ff{ve.x, ve.y}));
+      }
+      t = ff_norm(t);
+      V[e] = make_float2(t.h, t.l);
+      s2f = ff_add(s2f, ff_mul(t, t));
     }
   }
+  const double s2 = ff_to_double(s2f);
   if (!grid_sum_kv<KP, 1>(&s2, part, counter, tot) || threadIdx.x >= KP) return;
   // last block: plane rotation of right-hand side jj (Paige-Saunders)
   const int jj = threadIdx.x;
@@ -591,9 +605,9 @@ __global__ void __launch_bounds__(256) k_vec_a_b(int64_t n, const double* __rest
 }
 
 template <int KP>
-__global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const double* __restrict__ d,
-                                                 double* __restrict__ V, double* __restrict__ W,
-                                                 double* __restrict__ XZ,
+__global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __restrict__ d,
+                                                 float2* __restrict__ V, float2* __restrict__ W,
+                                                 float2* __restrict__ XZ,
                                                  float2* __restrict__ Vff,
                                                  const double* __restrict__ xref, double* sc,
                                                  double* part, unsigned int* counter, int first,
@@ -604,43 +618,51 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const double* __rest
   const int j = threadIdx.x % KP;
   const bool frozen = sc[B_DONE * KP + j] != 0.0 || j >= (int)g[G_K];
   const double alpha = sc[B_ALPHA * KP + j];
-  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-  const double rho = first ? 1.0 : sc[B_RHO * KP + j];
-  const double irho = 1.0 / rho;
-  const double t1 = first ? 0.0 : sc[B_T1 * KP + j], t2 = first ? 0.0 : sc[B_T2 * KP + j];
-  double acc[3] = {0.0, 0.0, 0.0};  // ||d_k||^2, ||x||^2, ||x - x_ref||^2
+  const ff ia = ff_from_double(alpha > 0.0 ? 1.0 / alpha : 0.0);
+  const ff irho = ff_from_double(first ? 1.0 : 1.0 / sc[B_RHO * KP + j]);
+  const ff t1 = ff_from_double(first ? 0.0 : sc[B_T1 * KP + j]);
+  const ff t2 = ff_from_double(first ? 0.0 : sc[B_T2 * KP + j]);
+  ff dk2f = ff_zero(), x2f = ff_zero();  // ||d_k||^2, ||x||^2
+  double e2 = 0.0;                       // ||x - x_ref||^2
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double dj = d[e / KP];
-    double xv;
+    const float2 djf = d[e / KP];
+    const ff dj = ff{djf.x, djf.y};
+    ff xv = ff_zero();
     if (frozen) {
       Vff[e] = make_float2(0.f, 0.f);
-      xv = first ? 0.0 : dj * XZ[e];
-    } else {
-      const double vn = V[e] * ia;
-      if (first) {
-        W[e] = vn;
-        XZ[e] = 0.0;
-        xv = 0.0;
-      } else {
-        const double wj = W[e];
-        const double dk = wj * irho;
-        acc[0] = __fma_rn(dk, dk, acc[0]);
-        const double xn = __fma_rn(t1, wj, XZ[e]);
-        XZ[e] = xn;
-        W[e] = __fma_rn(t2, wj, vn);
-        xv = dj * xn;
+      if (!first) {
+        const float2 xf = XZ[e];
+        xv = ff_norm(ff_mul(dj, ff{xf.x, xf.y}));
       }
-      V[e] = vn;
-      const ff f = ff_from_double(dj * vn);
+    } else {
+      const float2 vf = V[e];
+      const ff vn = ff_norm(ff_mul(ff{vf.x, vf.y}, ia));
+      if (first) {
+        W[e] = make_float2(vn.h, vn.l);
+        XZ[e] = make_float2(0.f, 0.f);
+      } else {
+        const float2 wf = W[e], xf = XZ[e];
+        const ff wj = ff{wf.x, wf.y};
+        const ff dk = ff_mul(wj, irho);
+        dk2f = ff_add(dk2f, ff_mul(dk, dk));
+        const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
+        XZ[e] = make_float2(xn.h, xn.l);
+        const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
+        W[e] = make_float2(wn.h, wn.l);
+        xv = ff_norm(ff_mul(dj, xn));
+      }
+      V[e] = make_float2(vn.h, vn.l);
+      const ff f = ff_norm(ff_mul(dj, vn));
       Vff[e] = make_float2(f.h, f.l);
     }
-    acc[1] = __fma_rn(xv, xv, acc[1]);
+    x2f = ff_add(x2f, ff_mul(xv, xv));
     if (xref) {
-      const double ex = xv - xref[e];
-      acc[2] = __fma_rn(ex, ex, acc[2]);
+      const double ex = ff_to_double(xv) - xref[e];
+      e2 = __fma_rn(ex, ex, e2);
     }
   }
+  double acc[3] = {ff_to_double(dk2f), ff_to_double(x2f), e2};
   if (!grid_sum_kv<KP, 3>(acc, part, counter, tot)) return;
   const int K = (int)g[G_K];
   if (first) {
@@ -705,15 +727,17 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const double* __rest
 
 // x_j = D z_j into the caller layout [n][k].
 __global__ void k_finish_b(int64_t n, int k, int KP, const double* __restrict__ d,
-                           const double* __restrict__ XZ, double* __restrict__ x) {
+                           const float2* __restrict__ XZ, double* __restrict__ x) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / k;
-    x[e] = d[i] * XZ[i * KP + e % k];
+    const float2 z = XZ[i * KP + e % k];
+    x[e] = d[i] * ff_to_double(ff{z.x, z.y});
   }
 }
 __global__ void k_scale_b(int64_t n, int mode, const double* __restrict__ colnorm,
-                          const double* __restrict__ user, double* __restrict__ dsc) {
+                          const double* __restrict__ user, double* __restrict__ dsc,
+                          float2* __restrict__ dsc_ff) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double s = 1.0;
@@ -724,6 +748,8 @@ __global__ void k_scale_b(int64_t n, int mode, const double* __restrict__ colnor
       s = user[j];
     }
     dsc[j] = s;
+    const ff f = ff_from_double(s);
+    dsc_ff[j] = make_float2(f.h, f.l);
   }
 }
 
@@ -736,7 +762,8 @@ struct BatchWork {
   int KP = 0;
   int64_t n_rows = 0, n_unk = 0;
   float2 *U = nullptr, *Uk = nullptr, *Vff = nullptr;
-  double *V = nullptr, *W = nullptr, *XZ = nullptr, *Z = nullptr, *D = nullptr;
+  float2 *V = nullptr, *W = nullptr, *XZ = nullptr, *Dff = nullptr;  // float pairs
+  double *Z = nullptr, *D = nullptr;
   double *sc = nullptr, *hsc = nullptr, *part = nullptr;
   unsigned int* count = nullptr;
   int threads = 256;  // block width of the row/knot kernels (tuned)
@@ -747,8 +774,8 @@ struct BatchWork {
 static void free_batch(BatchWork* w) {
   if (!w) return;
   void* p[] = {w->U,    w->Uk,   w->Vff,        w->V,          w->W,          w->XZ,
-               w->Z,    w->D,    w->sc,         w->part,       w->count,      w->csc.off,
-               w->csc.row, w->csc.val, w->csc.cnt};
+               w->Z,    w->D,    w->Dff,        w->sc,         w->part,       w->count,
+               w->csc.off, w->csc.row, w->csc.val, w->csc.cnt};
   for (void* q : p)
     if (q) cudaFree(q);
   if (w->hsc) cudaFreeHost(w->hsc);
@@ -835,6 +862,7 @@ static int batch_work(gsr_system* s, int KP, BatchWork** out, cudaStream_t st) {
   A((void**)&w->XZ, m * KP * 8);
   A((void**)&w->Z, m * KP * 8);
   A((void**)&w->D, m * 8);
+  A((void**)&w->Dff, m * 8);
   A((void**)&w->sc, (B_COUNT * KP + G_COUNT) * 8);
   A((void**)&w->part, (size_t)148 * 16 * 3 * 32 * 8);
   A((void**)&w->count, 16 * 4);
@@ -876,7 +904,7 @@ static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const 
   if (L.n_rows <= 0) return GSR_OK;
   if (cudaEventRecord(s->ev_fork, st) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(s->side, s->ev_fork, 0) != cudaSuccess) return GSR_E_CUDA;
-  const int att_blocks = (L.n_att_warps + 7) / 8;
+  const int att_blocks = (L.n_att_warps * ATT_B_SPLIT + 7) / 8;
   if (att_blocks > 0) k_aprod2_att_b<KP><<<att_blocks, 256, 0, s->side>>>(L, Yk, X, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   const InstrCsc& C = w->csc;
@@ -976,8 +1004,8 @@ static int enqueue_b(gsr_system* s, BatchWork* w, const double* xref, double* er
   k_zero_d<<<vb, 256, 0, st>>>(w->Z, m * KP, first ? nullptr : stop);
   rc = aprod2_b(s, w, w->U, w->Uk, w->Z, first ? nullptr : stop, st);
   if (rc != GSR_OK) return rc;
-  k_vec_a_b<KP><<<vb, 256, 0, st>>>(m, w->D, w->Z, w->V, w->sc, w->part, w->count + 1, first);
-  k_vec_b_b<KP><<<vb, 256, 0, st>>>(m, w->D, w->V, w->W, w->XZ, w->Vff, first ? nullptr : xref,
+  k_vec_a_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->Z, w->V, w->sc, w->part, w->count + 1, first);
+  k_vec_b_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->V, w->W, w->XZ, w->Vff, first ? nullptr : xref,
                                     w->sc, w->part, w->count + 2, first, first ? nullptr : err_dev);
   return cuda_status(cudaGetLastError());
 }
@@ -1024,7 +1052,7 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
     if (e == cudaSuccess) e = x;
   };
   const int vb = (int)std::min<int64_t>((m + 255) / 256, (int64_t)s->num_sms * 8);
-  k_scale_b<<<vb, 256, 0, st>>>(m, o->precond, s->colnorm, o->scale, w->D);
+  k_scale_b<<<vb, 256, 0, st>>>(m, o->precond, s->colnorm, o->scale, w->D, w->Dff);
   // the autotuner runs once per system and k, on the (so far unused) work vectors
   if (!w->tuned) {
     C(cudaMemsetAsync(w->Vff, 0, m * KP * 8, st));

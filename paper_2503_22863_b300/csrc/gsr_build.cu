@@ -15,7 +15,7 @@
 #include <thread>
 #include <vector>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace gsr {
 
@@ -116,7 +116,7 @@ void free_system(gsr_system* s) {
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
                   s->att_warp_knot, s->ct_round, s->round_entry, s->ient_ff, s->ient_f32,
                   s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
-                  s->dscale, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
+                  s->dscale, s->dscale_ff, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
                   s->S.count, s->S.x_ff, s->S.x3,
                   s->S.y_ff, s->S.y_knot, s->instr_count};
   for (void* p : ptrs)
@@ -292,8 +292,18 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     for (int64_t r = 0; r < n; ++r) pos[r] = (int32_t)(next[s_knot[r]]++);
   }
   // ---- instrumental tiles: the largest that fits the kernel's shared memory ----
-  int ct = CT_ROWS_MAX;
-  while (ct > REC_ROWS && instr_smem_bytes(ct, d.n_instr, false) > INSTR_SMEM_BUDGET) ct >>= 1;
+  // Tile height: larger tiles mean fewer, fuller rounds per entry, so take the
+  // largest tile either of two configurations fits, and between equal tiles
+  // prefer two single-buffered 256-thread blocks per SM (one block's barrier
+  // waits overlap the other's work) over one double-buffered 512-thread block.
+  int ct2 = 0, ct1 = 0;
+  for (int c = CT_ROWS_MAX; c >= 256 && ct2 == 0; c >>= 1)
+    if (instr_smem_bytes(c, d.n_instr, false, 1) <= INSTR_SMEM_HALF) ct2 = c;
+  for (int c = CT_ROWS_MAX; c >= REC_ROWS && ct1 == 0; c >>= 1)
+    if (instr_smem_bytes(c, d.n_instr, false, 2) <= INSTR_SMEM_BUDGET) ct1 = c;
+  const bool two_per_sm = ct2 > 0 && ct2 >= ct1;
+  const int ct = two_per_sm ? ct2 : (ct1 > 0 ? ct1 : REC_ROWS);
+  const int ct_bufs = two_per_sm ? 1 : 2, ct_per_sm = two_per_sm ? 2 : 1;
   InstrRounds ir;
   build_instr_rounds(d, vals, instr, ct, want_f32, nt, ir);
 
@@ -319,6 +329,8 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.instr_base = L.att_base + 3 * d.n_knots;
   L.glob_col = L.instr_base + d.n_instr;
   L.ct_rows = ct;
+  L.ct_bufs = ct_bufs;
+  L.ct_per_sm = ct_per_sm;
   L.n_ctiles = (int64_t)ir.ct_round.size() - 1;
 
   L.n_att_warps = sys->num_sms * 8;  // one 8-warp block per SM (the kernel holds ~180 registers)

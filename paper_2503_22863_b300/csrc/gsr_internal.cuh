@@ -16,13 +16,21 @@ constexpr int MAX_HIST_INSTR = 24576;  // instrumental bins of one block's histo
 constexpr int INSTR_BIN_BITS = 15;     // bin field of an instrumental entry key
 constexpr int INSTR_SMEM_BUDGET = 220 * 1024;  // dynamic shared memory of the instr kernel
 
-// Shared memory of the instrumental kernel for a tile of ct_rows rows:
-// keys (4 B) and coefficients (8 B pair / 4 B FP32) of 6 entries per row,
-// u of the tile as pairs (8 B per row) and the float-pair histogram.
-__host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t n_instr,
-                                                       bool f32) {
-  return 6 * ct_rows * 4 + 6 * ct_rows * (f32 ? 4 : 8) + ct_rows * 8 + n_instr * 8;
+// One tile buffer of the instrumental kernel for ct_rows rows: keys (4 B) and
+// coefficients (8 B pair / 4 B FP32) of 6 entries per row and u of the tile
+// as pairs (8 B per row). Every part is a multiple of 16 bytes for ct_rows >= 64.
+__host__ __device__ constexpr int64_t instr_tile_bytes(int64_t ct_rows, bool f32) {
+  return 6 * ct_rows * 4 + 6 * ct_rows * (f32 ? 4 : 8) + ct_rows * 8;
 }
+// Shared memory of the instrumental kernel: nbuf tile buffers (with two, the
+// next tile streams in while the current one is processed) and the float-pair
+// histogram.
+__host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t n_instr,
+                                                       bool f32, int nbuf) {
+  return nbuf * instr_tile_bytes(ct_rows, f32) + n_instr * 8;
+}
+// Two blocks of the instrumental kernel share an SM when each fits this much.
+constexpr int INSTR_SMEM_HALF = 112 * 1024;
 
 // ---------------------------------------------------------------------------
 // Row records. One record = 64 consecutive rows, everything aprod 1 needs for
@@ -213,6 +221,9 @@ struct Layout {
   // instrumental entries of each tile of ct_rows rows, in rounds of distinct bins
   int64_t n_ctiles;
   int32_t ct_rows;                      // power of two in [64, 2048]
+  int32_t ct_bufs;                      // tile buffers per block (2: double-buffered)
+  int32_t ct_per_sm;                    // blocks per SM: 2 (256 threads, 1 buffer) or
+                                        // 1 (512 threads, 2 buffers)
   const int32_t* ct_round;              // [n_ctiles + 1] first round of each tile
   const int64_t* round_entry;           // [n_rounds + 1] first entry of each round
   const float2* ient_ff;                // [6 n_rows] coefficient (pair)
@@ -231,88 +242,4 @@ struct Scratch {
   float2* y_knot;       // [n_rows] the same in knot order
 };
 
-}  // namespace gsr
-
-struct gsr_system {
-  int device;
-  int num_sms;
-  gsr_dims dims;
-  gsr::Layout L;
-  gsr::Scratch S;
-  // owned allocations
-  unsigned char* rec_ff;
-  unsigned char* rec_f32;
-  int32_t* pos;
-  float2* att_knot_ff;
-  float* att_knot_f32;
-  int64_t* knot_start;
-  int32_t* att_warp_knot;
-  int32_t* ct_round;
-  int64_t* round_entry;
-  float2* ient_ff;
-  float* ient_f32;
-  uint32_t* ient_key;
-  int* err;
-  double* colnorm;       // [n_unk] ||A_:,j|| (FP64 values)
-  // LSQR work vectors (allocated on first solve)
-  float2* u;             // [n_pad] unnormalised u as float pairs (zero padding)
-  float2* u_knot;        // [n_rows] u in knot order
-  double* v;             // [n_unk]
-  double* w;             // [n_unk]
-  double* xz;            // [n_unk] iterate of the scaled problem
-  double* z;             // [n_unk] A^T u accumulator
-  double* dscale;        // [n_unk] column scaling in use
-  float2* v_ff;          // [n_unk] float-pair D v (aprod 1 input)
-  double* mx_x1;         // mixed precision: phase-1 solution [n_unk]
-  double* mx_d;          // mixed precision: correction [n_unk]
-  double* mx_r;          // mixed precision: residual b - A x1 [n_rows]
-  double* scal;          // device LSQR scalars
-  double* host_scal;     // pinned mirror of scal
-  void* batch;           // multi-right-hand-side workspace (allocated on first use)
-  int* instr_count;      // [n_instr] rows per instrumental column (learned features)
-  cudaStream_t side;     // second stream for the attitude part of aprod 2
-  cudaEvent_t ev_fork, ev_join;
-  int main_block, main_ctas, main_smem;
-  int a1_ctas;
-};
-
-// Internal entry points shared between translation units.
-namespace gsr {
-// Rows padded up to a whole number of instrumental tiles (float-pair vectors
-// over the rows are allocated with this length, the padding zeroed).
-inline int64_t padded_rows(const Layout& L) {
-  const int64_t ct = L.ct_rows > 0 ? L.ct_rows : REC_ROWS;
-  return ((L.n_rows + ct - 1) / ct) * ct + REC_ROWS;
-}
-// y = coef*y + A x on a double y (coef = *coef_dev if non-null), ||y||^2 into
-// *norm_slot; y_knot must be null. The kernel does nothing when *stop != 0.
-// The attitude unknowns are gathered from x_ff directly (no scratch).
-int launch_aprod1(gsr_system* sys, int which_values, const float2* x_ff, double* y,
-                  const double* coef_dev, double coef_host, double* y_knot, double* norm_slot,
-                  const double* stop, cudaStream_t st);
-// y += A x on a double y, the attitude unknowns read from sys->S.x3 (built by
-// launch_att_x3 from the same x_ff).
-int launch_aprod1_x3(gsr_system* sys, int which_values, const float2* x_ff, double* y,
-                     cudaStream_t st);
-// y = coef*y + A x on a float-pair y (LSQR's u), attitude from sys->S.x3, with
-// the optional knot-order copy.
-int launch_aprod1_ff(gsr_system* sys, int which_values, const float2* x_ff, float2* y,
-                     const double* coef_dev, float2* y_knot, double* norm_slot,
-                     const double* stop, cudaStream_t st);
-// x += A^T y, y and y_knot (y in knot order) as float pairs, y zero-padded to
-// padded_rows(); nothing when *stop != 0.
-int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const float2* y_knot,
-                  double* x, const double* stop, cudaStream_t st);
-int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, cudaStream_t st);
-// out = -x as float pairs.
-int launch_to_ff_neg(const double* x, float2* out, int64_t n, cudaStream_t st);
-// Interleave the attitude part of a float-pair aprod 1 input by start knot
-// (into sys->S.x3); aprod 1 reads it with three 32-byte loads per row.
-int launch_att_x3(gsr_system* sys, const float2* x_ff, const double* stop, cudaStream_t st);
-// y (double) -> y_ff (row order) and y_knot (knot order) as float pairs.
-int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
-                      cudaStream_t st);
-int cuda_status(cudaError_t e);
-int set_kernel_attributes();
-void destroy_batch(gsr_system* s);
 }  // namespace gsr

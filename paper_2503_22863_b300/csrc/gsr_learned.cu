@@ -15,7 +15,7 @@
 #include <cmath>
 #include <cstdint>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace gsr {
 

@@ -18,7 +18,7 @@
 #include <cstring>
 #include <vector>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace gsr {
 
@@ -111,20 +111,26 @@ __global__ void k_init_u(Layout L, const double* __restrict__ b, float2* __restr
 // vec_a: v~ = d z / beta - beta v (v absent on the first call); ||v~||^2;
 // then (last block) the scalar step.
 // ---------------------------------------------------------------------------
-__global__ void k_vec_a(int64_t n, const double* __restrict__ d, const double* __restrict__ z,
-                        double* __restrict__ v, double* scal, double* part, unsigned int* counter,
+__global__ void k_vec_a(int64_t n, const float2* __restrict__ d, const double* __restrict__ z,
+                        float2* __restrict__ v, double* scal, double* part, unsigned int* counter,
                         int first) {
   if (scal[S_DONE] != 0.0) return;
   const double beta = sqrt(scal[S_UNORM2]);
-  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
-  double s2 = 0.0, z0 = 0.0, z1 = 0.0;
+  const ff ib = ff_from_double(beta > 0.0 ? 1.0 / beta : 0.0), nbeta = ff_from_double(-beta);
+  ff s2f = ff_zero();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
-    double t = d[j] * z[j] * ib;
-    if (!first) t = __fma_rn(-beta, v[j], t);
-    v[j] = t;
-    s2 = __fma_rn(t, t, s2);
+    const float2 dj = d[j];
+    ff t = ff_mul(ff_norm(ff_mul(ff{dj.x, dj.y}, ff_from_double(z[j]))), ib);
+    if (!first) {
+      const float2 vj = v[j];
+      t = ff_add(t, ff_mul(nbeta, ff{vj.x, vj.y}));
+    }
+    t = ff_norm(t);
+    v[j] = make_float2(t.h, t.l);
+    s2f = ff_add(s2f, ff_mul(t, t));
   }
+  double s2 = ff_to_double(s2f), z0 = 0.0, z1 = 0.0;
   if (!grid_sum3(s2, z0, z1, part, counter) || threadIdx.x != 0) return;
   const double alpha = sqrt(s2);
   if (first) {
@@ -166,47 +172,53 @@ __global__ void k_vec_a(int64_t n, const double* __restrict__ d, const double* _
 // vec_b: normalise v, update x and w, write D v as float pairs, ||x||,
 // ||d_k||^2 and the variance; then (last block) the stopping tests.
 // ---------------------------------------------------------------------------
-__global__ void k_vec_b(int64_t n, const double* __restrict__ d, double* __restrict__ v,
-                        double* __restrict__ w, double* __restrict__ xz,
+__global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restrict__ v,
+                        float2* __restrict__ w, float2* __restrict__ xz,
                         float2* __restrict__ v_ff, double* __restrict__ var,
                         const double* __restrict__ x_ref, const double* __restrict__ x_off,
                         double* scal, double* part, unsigned int* counter, int first,
                         double* err_hist, double* rnorm_hist) {
   if (scal[S_DONE] != 0.0) return;
   const double alpha = scal[S_ALPHA];
-  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-  const double rho = first ? 1.0 : scal[S_RHO];
-  const double irho = 1.0 / rho;
-  const double t1 = first ? 0.0 : scal[S_T1], t2 = first ? 0.0 : scal[S_T2];
-  double dk2 = 0.0, x2 = 0.0, e2 = 0.0;
+  const ff ia = ff_from_double(alpha > 0.0 ? 1.0 / alpha : 0.0);
+  const ff irho = ff_from_double(first ? 1.0 : 1.0 / scal[S_RHO]);
+  const ff t1 = ff_from_double(first ? 0.0 : scal[S_T1]);
+  const ff t2 = ff_from_double(first ? 0.0 : scal[S_T2]);
+  ff dk2f = ff_zero(), x2f = ff_zero();
+  double e2 = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const double vn = v[j] * ia;
-    const double dj = d[j];
-    double xv;
+    const float2 vj = v[j], djf = d[j];
+    const ff dj = ff{djf.x, djf.y};
+    const ff vn = ff_norm(ff_mul(ff{vj.x, vj.y}, ia));
+    ff xv = ff_zero();
     if (first) {
-      w[j] = vn;
-      xz[j] = 0.0;
-      xv = 0.0;
+      w[j] = make_float2(vn.h, vn.l);
+      xz[j] = make_float2(0.f, 0.f);
     } else {
-      const double wj = w[j];
-      const double dk = wj * irho;
-      dk2 = __fma_rn(dk, dk, dk2);
-      if (var) var[j] = __fma_rn(dk, dk, var[j]);
-      const double xn = __fma_rn(t1, wj, xz[j]);
-      xz[j] = xn;
-      w[j] = __fma_rn(t2, wj, vn);
-      xv = dj * xn;
-      x2 = __fma_rn(xv, xv, x2);
+      const float2 wf = w[j], xf = xz[j];
+      const ff wj = ff{wf.x, wf.y};
+      const ff dk = ff_mul(wj, irho);
+      const ff dd = ff_mul(dk, dk);
+      dk2f = ff_add(dk2f, dd);
+      if (var) var[j] += ff_to_double(dd);
+      const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
+      xz[j] = make_float2(xn.h, xn.l);
+      const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
+      w[j] = make_float2(wn.h, wn.l);
+      xv = ff_norm(ff_mul(dj, xn));
+      x2f = ff_add(x2f, ff_mul(xv, xv));
     }
-    v[j] = vn;
-    const ff f = ff_from_double(dj * vn);
+    v[j] = make_float2(vn.h, vn.l);
+    const ff f = ff_norm(ff_mul(dj, vn));
     v_ff[j] = make_float2(f.h, f.l);
     if (x_ref) {
-      const double e = (x_off ? xv + x_off[j] : xv) - x_ref[j];
+      const double xd = ff_to_double(xv);
+      const double e = (x_off ? xd + x_off[j] : xd) - x_ref[j];
       e2 = __fma_rn(e, e, e2);
     }
   }
+  double dk2 = ff_to_double(dk2f), x2 = ff_to_double(x2f);
   if (!grid_sum3(dk2, x2, e2, part, counter) || threadIdx.x != 0) return;
   if (first) return;
   const double itn = scal[S_ITN] + 1.0;
@@ -257,7 +269,8 @@ __global__ void k_sumsq(int64_t n, const double* __restrict__ a, double* scal, i
 }
 
 __global__ void k_scale_setup(int64_t n, int mode, const double* __restrict__ colnorm,
-                              const double* __restrict__ user, double* __restrict__ d) {
+                              const double* __restrict__ user, double* __restrict__ d,
+                              float2* __restrict__ d_ff) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double s = 1.0;
@@ -268,16 +281,19 @@ __global__ void k_scale_setup(int64_t n, int mode, const double* __restrict__ co
       s = user[j];
     }
     d[j] = s;
+    const ff f = ff_from_double(s);
+    d_ff[j] = make_float2(f.h, f.l);
   }
 }
 
 // x = D z (de-precondition, Sec. 2 solver step 5); var = D^2 var.
-__global__ void k_finish(int64_t n, const double* __restrict__ d, const double* __restrict__ xz,
+__global__ void k_finish(int64_t n, const double* __restrict__ d, const float2* __restrict__ xz,
                          double* __restrict__ x, double* __restrict__ var) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const double dj = d[j];
-    x[j] = dj * xz[j];
+    const float2 z = xz[j];
+    x[j] = dj * ff_to_double(ff{z.x, z.y});
     if (var) var[j] *= dj * dj;
   }
 }
@@ -305,6 +321,7 @@ int ensure_work(gsr_system* s) {
   A((void**)&s->xz, m * 8);
   A((void**)&s->z, m * 8);
   A((void**)&s->dscale, m * 8);
+  A((void**)&s->dscale_ff, m * 8);
   A((void**)&s->v_ff, m * 8);
   A((void**)&s->scal, S_COUNT * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_scal, S_COUNT * 8);
@@ -346,8 +363,9 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   rc = launch_aprod2(s, c.which_values, s->u, s->u_knot, s->z, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
   if (ev) cudaEventRecordWithFlags(ev[2], c.st, cudaEventRecordExternal);
-  k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 0);
-  k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
+  k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->z, s->v, scal, s->S.red,
+                                s->S.count + 1, 0);
+  k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
                                 c.x_off, scal, s->S.red, s->S.count + 2, 0, c.err_dev, c.rn_dev);
   if (ev) cudaEventRecordWithFlags(ev[3], c.st, cudaEventRecordExternal);
   return cuda_status(cudaGetLastError());
@@ -387,14 +405,15 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (o->x_ref && err_dev)
     k_sumsq<<<vb, 256, 0, st>>>(L.n_unk, o->x_ref, scal, S_XREF2, s->S.red, s->S.count + 3);
   if (o->var) k_zero<<<vb, 256, 0, st>>>(L.n_unk, o->var, nullptr);
-  k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->xz, nullptr);
+  k_zero<<<vb, 256, 0, st>>>(L.n_unk, reinterpret_cast<double*>(s->xz), nullptr);
   // start: beta_1 u_1 = b, alpha_1 v_1 = (A D)^T u_1, w_1 = v_1, x_0 = 0
   k_init_u<<<rb, 256, 0, st>>>(L, b, s->u, s->u_knot, scal, s->S.red, s->S.count + 4);
   k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->z, nullptr);
   int rc = launch_aprod2(s, which_values, s->u, s->u_knot, s->z, nullptr, st);
   if (rc != GSR_OK) return rc;
-  k_vec_a<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->z, s->v, scal, s->S.red, s->S.count + 1, 1);
-  k_vec_b<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->v, s->w, s->xz, s->v_ff, o->var,
+  k_vec_a<<<vb, 256, 0, st>>>(L.n_unk, s->dscale_ff, s->z, s->v, scal, s->S.red, s->S.count + 1,
+                              1);
+  k_vec_b<<<vb, 256, 0, st>>>(L.n_unk, s->dscale_ff, s->v, s->w, s->xz, s->v_ff, o->var,
                               o->x_ref && err_dev ? o->x_ref : nullptr, x_off, scal, s->S.red,
                               s->S.count + 2, 1, nullptr, nullptr);
   C(cudaGetLastError());
@@ -589,7 +608,8 @@ int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o
 
 int setup_scaling(gsr_system* s, const gsr_lsqr_opts* o, cudaStream_t st) {
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (s->L.n_unk + 255) / 256 + 1);
-  k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->dscale);
+  k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->dscale,
+                                    s->dscale_ff);
   return cuda_status(cudaGetLastError());
 }
 

@@ -15,7 +15,7 @@
 // every GPU that loads the library keeps reserved until the process exits.
 #include <mutex>
 
-#include "gsr_internal.cuh"
+#include "gsr_system.cuh"
 
 namespace {
 
