@@ -366,6 +366,17 @@ def bench_learned(args, dev):
             "train_s": t_train, "label_search_s": t_lab, "eval_s": t_eval}
 
 
+def max_over_ranks(vals, dist, device):
+    """Element-wise maximum of per-rank values over all ranks (identity for one
+    process): with independent replicas the job takes as long as its slowest rank."""
+    if dist is None:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -453,13 +464,8 @@ def run_ours(args):
             if args.learned_systems > 0:
                 variants["learned"] = bench_learned(args, dev)
 
-    ms = float(np.mean(step_ms))
-    if dist is not None:
-        t = torch.tensor([ms, float(np.median(e2e))], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
-    else:
-        e2e_s = float(np.median(e2e))
+    # replicas: the job's time is that of its slowest rank
+    ms, e2e_s = max_over_ranks([float(np.mean(step_ms)), float(np.median(e2e))], dist, dev)
 
     nt = sum(r["n_timed_itn"] for r in results)
     t_a1 = sum(r["t_aprod1_ms"] for r in results) / max(nt, 1)
