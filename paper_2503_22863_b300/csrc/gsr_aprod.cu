@@ -153,6 +153,8 @@ __device__ __forceinline__ ff val_mul(ff v, ff u) {
 // One CTA per SM, NW warps; each warp owns NS record buffers in shared memory
 // that lane 0 refills with TMA while the warp computes on the previous one.
 // ---------------------------------------------------------------------------
+constexpr int A1_PF = 1;  // records a warp keeps in flight towards L2 beyond its buffers
+
 template <bool F32, bool YFF, bool X3, int NW, int NS>
 __global__ void __launch_bounds__(NW * 32, 1)
     k_aprod1(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
@@ -191,6 +193,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
         mbar_expect_tx(&bar[s], R::BYTES);
         tma_load(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s]);
       }
+    }
+#pragma unroll
+    for (int k = 0; k < A1_PF; ++k) {
+      const int64_t rp = gw + (NS + k) * nw;
+      if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
     }
   }
   __syncwarp();
@@ -342,6 +349,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
         mbar_expect_tx(&bar[s], R::BYTES);
         tma_load(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s]);
       }
+      // A1_PF records further ahead go to L2 only, so that the copies find
+      // their records there when their turn comes
+      const int64_t rp = rn + A1_PF * nw;
+      if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
     }
     s = (s + 1 == NS) ? 0 : s + 1;
   }
@@ -520,51 +531,59 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
   __shared__ __align__(8) uint64_t bar[2];
   constexpr int VB = F32 ? 4 : 8;  // bytes per entry coefficient
   const int CT = L.ct_rows;
-  const int64_t TB = instr_tile_bytes(CT, F32);
-  // [buffer 0 | buffer 1 | histogram n_instr pairs], a buffer being
-  // [keys 6*CT u32 | coefficients 6*CT | u pairs CT]
+  // block -> (column group g, first tile); the grid is a multiple of the groups
+  const int G = L.n_bgroups, g = blockIdx.x % G;
+  const int64_t T = gridDim.x / G;
+  const int bin_lo = g * L.bgroup_bins;
+  const int nb = min(L.bgroup_bins, (int)L.n_instr - bin_lo);
+  const int64_t KB = instr_keys_bytes(L.ct_max_ent), VBB = instr_vals_bytes(L.ct_max_ent, F32);
+  const int64_t TB = KB + VBB + (int64_t)CT * 8;
+  // [buffer 0 | buffer 1 | histogram of the group's columns], a buffer being
+  // [keys | coefficients | u pairs CT], keys and coefficients of one segment
   float2* hist = reinterpret_cast<float2*>(smem + NBUF * TB);
-  for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = make_float2(0.f, 0.f);
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_proxy_async();
   }
   __syncthreads();
-  // thread 0: start the copies of tile ct into buffer b
+  // thread 0: start the copies of segment (tile ct, group g) into buffer b
   auto issue = [&](int64_t ct, int b) {
     unsigned char* base = smem + b * TB;
-    const int64_t e0 = L.round_entry[L.ct_round[ct]], e1 = L.round_entry[L.ct_round[ct + 1]];
+    const int64_t c = ct * G + g;
+    const int64_t e0 = L.round_entry[L.ct_round[c]], e1 = L.round_entry[L.ct_round[c + 1] - 1];
     const int64_t ne = e1 - e0;
     fence_proxy_async();
-    // sizes rounded up to 16 bytes (the entry arrays are padded for this);
-    // u is padded to whole tiles, so the full tile is always in bounds
+    // sizes rounded up to 16 bytes (segments start 16-byte aligned and the
+    // entry arrays are padded); u is padded to whole tiles
     const uint32_t kb = (uint32_t)((ne * 4 + 15) & ~15LL);
     const uint32_t vb = (uint32_t)((ne * VB + 15) & ~15LL);
     const uint32_t ub = (uint32_t)CT * 8u;
     mbar_expect_tx(&bar[b], kb + vb + ub);
-    tma_load(base + 6 * CT * 4 + 6 * CT * VB, y + ct * CT, ub, &bar[b]);
+    tma_load(base + KB + VBB, y + ct * CT, ub, &bar[b]);
     if (ne > 0) {
       tma_load(base, L.ient_key + e0, kb, &bar[b]);
-      if constexpr (F32) tma_load(base + 6 * CT * 4, L.ient_f32 + e0, vb, &bar[b]);
-      else tma_load(base + 6 * CT * 4, L.ient_ff + e0, vb, &bar[b]);
+      if constexpr (F32) tma_load(base + KB, L.ient_f32 + e0, vb, &bar[b]);
+      else tma_load(base + KB, L.ient_ff + e0, vb, &bar[b]);
     }
   };
   uint32_t parity = 0u, pending = 0u;  // bit q: phase / copy in flight of buffer q
   bool ok = true;
   int b = 0;
-  if (NBUF == 2 && blockIdx.x < L.n_ctiles) {
-    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+  const int64_t t0 = blockIdx.x / G;
+  if (NBUF == 2 && t0 < L.n_ctiles) {
+    if (threadIdx.x == 0) issue(t0, 0);
     pending = 1u;
   }
-  for (int64_t ct = blockIdx.x; ct < L.n_ctiles; ct += gridDim.x, b ^= (NBUF - 1)) {
+  for (int64_t ct = t0; ct < L.n_ctiles; ct += T, b ^= (NBUF - 1)) {
     // the buffer written here was last read by the previous tile, which ended
     // in a barrier
     if (NBUF == 1) {
       if (threadIdx.x == 0) issue(ct, 0);
       pending = 1u;
-    } else if (ct + gridDim.x < L.n_ctiles) {
-      if (threadIdx.x == 0) issue(ct + gridDim.x, b ^ 1);
+    } else if (ct + T < L.n_ctiles) {
+      if (threadIdx.x == 0) issue(ct + T, b ^ 1);
       pending |= 1u << (b ^ 1);
     }
     bool got = false;
@@ -581,16 +600,17 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     parity ^= 1u << b;
     pending &= ~(1u << b);
     const uint32_t* keys = reinterpret_cast<const uint32_t*>(smem + b * TB);
-    const unsigned char* vals = smem + b * TB + 6 * CT * 4;
-    const float2* us = reinterpret_cast<const float2*>(vals + 6 * CT * VB);
-    const int k0 = L.ct_round[ct], k1 = L.ct_round[ct + 1];
+    const unsigned char* vals = smem + b * TB + KB;
+    const float2* us = reinterpret_cast<const float2*>(smem + b * TB + KB + VBB);
+    const int64_t c = ct * G + g;
+    const int k0 = L.ct_round[c], k1 = L.ct_round[c + 1] - 1;  // the last slot ends the segment
     const int64_t e0 = L.round_entry[k0];
     for (int k = k0; k < k1; ++k) {
       const int a = (int)(L.round_entry[k] - e0), bb = (int)(L.round_entry[k + 1] - e0);
       for (int e = a + threadIdx.x; e < bb; e += blockDim.x) {
         const uint32_t key = keys[e];
         const int row = (int)(key >> INSTR_BIN_BITS);
-        const int bin = (int)(key & ((1u << INSTR_BIN_BITS) - 1));
+        const int bin = (int)(key & ((1u << INSTR_BIN_BITS) - 1)) - bin_lo;
         const float2 uu = us[row];
         ff p;
         if constexpr (F32) {
@@ -614,9 +634,9 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
           if (mbar_try_wait(&bar[q], (parity >> q) & 1u)) break;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     const float2 h = hist[i];
-    red_ff(x + L.instr_base + i, ff{h.x, h.y});
+    red_ff(x + L.instr_base + bin_lo + i, ff{h.x, h.y});
   }
 }
 
@@ -848,9 +868,13 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
     else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
-  const int ib = (int)std::min<int64_t>((int64_t)sys->num_sms * L.ct_per_sm, L.n_ctiles);
-  const int ismem = (int)instr_smem_bytes(L.ct_rows, L.n_instr, f32, L.ct_bufs);
-  if (ib > 0) {
+  // G column groups, each over tile streams of num_sms * per_sm / G blocks
+  const int64_t per_group = std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sys->num_sms * L.ct_per_sm / L.n_bgroups, L.n_ctiles));
+  const int ib = (int)(per_group * L.n_bgroups);
+  const int ismem =
+      (int)instr_smem_bytes(L.ct_rows, L.ct_max_ent, L.bgroup_bins, f32, L.ct_bufs);
+  if (L.n_ctiles > 0) {
     if (L.ct_per_sm == 1) {
       if (f32) k_aprod2_instr<true, 2, 512><<<ib, 512, ismem, st>>>(L, y, x, stop);
       else k_aprod2_instr<false, 2, 512><<<ib, 512, ismem, st>>>(L, y, x, stop);

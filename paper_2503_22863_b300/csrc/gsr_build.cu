@@ -169,38 +169,57 @@ void parallel_for(int64_t n, unsigned nt, F f) {
   for (auto& t : th) t.join();
 }
 
-// Instrumental entries of every tile of ct rows, ordered into rounds in which
-// each bin occurs at most once (round = earlier occurrences of the bin in the
-// tile), and by bin inside a round.
+// Instrumental entries of every tile of ct rows, split by column group (G
+// groups of bpg consecutive columns), each (tile, group) segment ordered into
+// rounds in which every column occurs at most once (round = earlier
+// occurrences of the column in the tile) and by column inside a round.
+// Segments are stored tile-major, each starting at a multiple of 4 entries.
+// Segment c owns round slots [ct_round[c], ct_round[c+1]); the last slot is a
+// terminator whose round_entry is the segment's exact end (the padding after
+// a segment belongs to no round).
 struct InstrRounds {
   std::vector<int32_t> ct_round;
   std::vector<int64_t> round_entry;
   std::vector<uint32_t> key;
   std::vector<float2> vff;
   std::vector<float> vf32;
+  int64_t max_ent = 0;
 };
 
 void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* instr, int ct,
-                        bool want_f32, unsigned nt, InstrRounds& out) {
+                        int G, int bpg, bool want_f32, unsigned nt, InstrRounds& out) {
   const int64_t n = d.n_rows;
   const int64_t n_ct = (n + ct - 1) / ct;
-  std::vector<int32_t> rounds(n_ct, 0);
+  const int64_t n_seg = n_ct * G;
+  std::vector<int32_t> rounds(n_seg, 0);
+  std::vector<int64_t> seg_n(n_seg, 0);
   std::vector<std::vector<int32_t>> occ(nt, std::vector<int32_t>(d.n_instr, 0));
   parallel_for(n_ct, nt, [&](int64_t t, unsigned w) {
     auto& o = occ[w];
     const int64_t a = t * ct, b = std::min<int64_t>(n, a + ct);
-    int mx = 0;
     for (int64_t i = a; i < b; ++i)
-      for (int k = 0; k < 6; ++k) mx = std::max(mx, ++o[instr[i * 6 + k]]);
+      for (int k = 0; k < 6; ++k) {
+        const int bin = instr[i * 6 + k];
+        const int g = bin / bpg;
+        rounds[t * G + g] = std::max(rounds[t * G + g], ++o[bin]);
+        ++seg_n[t * G + g];
+      }
     for (int64_t i = a; i < b; ++i)
       for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
-    rounds[t] = mx;
   });
-  out.ct_round.assign(n_ct + 1, 0);
-  for (int64_t t = 0; t < n_ct; ++t) out.ct_round[t + 1] = out.ct_round[t] + rounds[t];
-  const int64_t n_rounds = out.ct_round[n_ct];
-  const int64_t n_ent = 6 * n;
-  out.round_entry.assign(n_rounds + 1, n_ent);
+  std::vector<int64_t> seg_start(n_seg + 1, 0);
+  out.ct_round.assign(n_seg + 1, 0);
+  out.max_ent = 0;
+  for (int64_t c = 0; c < n_seg; ++c) {
+    out.ct_round[c + 1] = out.ct_round[c] + rounds[c] + 1;
+    seg_start[c + 1] = (seg_start[c] + seg_n[c] + 3) & ~3LL;  // next segment 16-B aligned
+    out.max_ent = std::max(out.max_ent, seg_n[c]);
+  }
+  const int64_t n_slots = out.ct_round[n_seg];
+  const int64_t n_ent = seg_start[n_seg];
+  out.round_entry.assign(n_slots + 1, n_ent);
+  for (int64_t c = 0; c < n_seg; ++c)  // terminators: exact segment ends
+    out.round_entry[out.ct_round[c + 1] - 1] = seg_start[c] + seg_n[c];
   out.key.assign(n_ent + 4, 0u);  // +4: TMA copies are rounded up to 16 bytes
   out.vff.assign(n_ent + 4, make_float2(0.f, 0.f));
   if (want_f32) out.vf32.assign(n_ent + 4, 0.f);
@@ -212,24 +231,30 @@ void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* in
     for (int64_t i = a; i < b; ++i)
       for (int k = 0; k < 6; ++k) {
         const int bin = instr[i * 6 + k];
+        const uint64_t g = (uint64_t)(bin / bpg);
         const uint64_t rnd = (uint64_t)o[bin]++;
-        order.push_back((rnd << 40) | ((uint64_t)bin << 24) | ((uint64_t)(i - a) << 3) |
-                        (uint64_t)k);
+        order.push_back((g << 58) | (rnd << 40) | ((uint64_t)bin << 24) |
+                        ((uint64_t)(i - a) << 3) | (uint64_t)k);
       }
     for (int64_t i = a; i < b; ++i)
       for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
     std::sort(order.begin(), order.end());
-    int64_t e = 6 * a;
-    int64_t kr = out.ct_round[t];
-    int64_t cur = -1;
+    int64_t cur_g = -1, cur_r = -1, e = 0, kr = 0;
     for (uint64_t v : order) {
-      const int64_t rnd = (int64_t)(v >> 40);
+      const int64_t g = (int64_t)(v >> 58);
+      const int64_t rnd = (int64_t)((v >> 40) & 0x3ffff);
       const uint32_t bin = (uint32_t)((v >> 24) & 0xffff);
       const int64_t row = (int64_t)((v >> 3) & 0x1fffff);
       const int k = (int)(v & 7);
-      if (rnd != cur) {
+      if (g != cur_g) {
+        e = seg_start[t * G + g];
+        kr = out.ct_round[t * G + g];
+        cur_g = g;
+        cur_r = -1;
+      }
+      if (rnd != cur_r) {
         out.round_entry[kr + rnd] = e;
-        cur = rnd;
+        cur_r = rnd;
       }
       out.key[e] = ((uint32_t)row << INSTR_BIN_BITS) | bin;
       const double x = vals[(a + row) * NSLOT + 17 + k];
@@ -239,6 +264,14 @@ void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* in
       ++e;
     }
   });
+}
+
+// Entries a (tile, group) segment is sized for before the exact count is known:
+// all 6 ct with one group, else the mean plus six standard deviations.
+int64_t est_seg_entries(int ct, int G) {
+  if (G == 1) return 6LL * ct;
+  const double m = 6.0 * ct / G;
+  return (int64_t)(m + 6.0 * std::sqrt(m)) + 8;
 }
 
 }  // namespace
@@ -291,21 +324,41 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     std::vector<int64_t> next(knot_start.begin(), knot_start.end() - 1);
     for (int64_t r = 0; r < n; ++r) pos[r] = (int32_t)(next[s_knot[r]]++);
   }
-  // ---- instrumental tiles: the largest that fits the kernel's shared memory ----
-  // Tile height: larger tiles mean fewer, fuller rounds per entry, so take the
-  // largest tile either of two configurations fits, and between equal tiles
-  // prefer two single-buffered 256-thread blocks per SM (one block's barrier
-  // waits overlap the other's work) over one double-buffered 512-thread block.
-  int ct2 = 0, ct1 = 0;
-  for (int c = CT_ROWS_MAX; c >= 256 && ct2 == 0; c >>= 1)
-    if (instr_smem_bytes(c, d.n_instr, false, 1) <= INSTR_SMEM_HALF) ct2 = c;
-  for (int c = CT_ROWS_MAX; c >= REC_ROWS && ct1 == 0; c >>= 1)
-    if (instr_smem_bytes(c, d.n_instr, false, 2) <= INSTR_SMEM_BUDGET) ct1 = c;
-  const bool two_per_sm = ct2 > 0 && ct2 >= ct1;
-  const int ct = two_per_sm ? ct2 : (ct1 > 0 ? ct1 : REC_ROWS);
-  const int ct_bufs = two_per_sm ? 1 : 2, ct_per_sm = two_per_sm ? 2 : 1;
+  // ---- instrumental tiles and column groups ----
+  // Larger tiles mean fewer, fuller rounds per entry. The columns are split
+  // into the fewest groups (each block holds one group's histogram) that still
+  // allow tiles of at least 1024 rows; then the largest tile wins, and between
+  // equal tiles two single-buffered 256-thread blocks per SM (one block's
+  // barrier waits overlap the other's work) beat one double-buffered
+  // 512-thread block. The sizes are checked against the exact segment counts.
   InstrRounds ir;
-  build_instr_rounds(d, vals, instr, ct, want_f32, nt, ir);
+  int ct = 0, G = 1, bpg = (int)d.n_instr, ct_bufs = 2, ct_per_sm = 1;
+  for (int g = 1; g <= 4; ++g) {
+    const int b = (int)((d.n_instr + g - 1) / g);
+    int c2 = 0, c1 = 0;
+    for (int c = CT_ROWS_MAX; c >= 256 && c2 == 0; c >>= 1)
+      if (instr_smem_bytes(c, est_seg_entries(c, g), b, false, 1) <= INSTR_SMEM_HALF) c2 = c;
+    for (int c = CT_ROWS_MAX; c >= REC_ROWS && c1 == 0; c >>= 1)
+      if (instr_smem_bytes(c, est_seg_entries(c, g), b, false, 2) <= INSTR_SMEM_BUDGET) c1 = c;
+    if (c1 == 0 && c2 == 0) continue;
+    const bool two = c2 > 0 && c2 >= c1;
+    ct = two ? c2 : c1;
+    G = g;
+    bpg = b;
+    ct_bufs = two ? 1 : 2;
+    ct_per_sm = two ? 2 : 1;
+    if (ct >= 1024) break;
+  }
+  if (ct == 0) return GSR_E_UNSUPPORTED;
+  for (;;) {
+    build_instr_rounds(d, vals, instr, ct, G, bpg, want_f32, nt, ir);
+    const int64_t lim = ct_per_sm == 2 ? INSTR_SMEM_HALF : INSTR_SMEM_BUDGET;
+    if (instr_smem_bytes(ct, ir.max_ent, bpg, false, ct_bufs) <= lim || ct <= REC_ROWS) break;
+    ct >>= 1;  // an unusually full segment: retry with shorter tiles
+  }
+  if (instr_smem_bytes(ct, ir.max_ent, bpg, false, ct_bufs) >
+      (ct_per_sm == 2 ? INSTR_SMEM_HALF : INSTR_SMEM_BUDGET))
+    return GSR_E_UNSUPPORTED;
 
   // host validation is done; everything below needs the device
   if (cudaSetDevice(device) != cudaSuccess) return GSR_E_CUDA;
@@ -329,9 +382,12 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.instr_base = L.att_base + 3 * d.n_knots;
   L.glob_col = L.instr_base + d.n_instr;
   L.ct_rows = ct;
+  L.n_bgroups = G;
+  L.bgroup_bins = bpg;
+  L.ct_max_ent = (int32_t)ir.max_ent;
   L.ct_bufs = ct_bufs;
   L.ct_per_sm = ct_per_sm;
-  L.n_ctiles = (int64_t)ir.ct_round.size() - 1;
+  L.n_ctiles = ((int64_t)ir.ct_round.size() - 1) / G;
 
   L.n_att_warps = sys->num_sms * 8;  // one 8-warp block per SM (the kernel holds ~180 registers)
   std::vector<int32_t> att_warp_knot(L.n_att_warps + 1);

@@ -16,18 +16,25 @@ constexpr int MAX_HIST_INSTR = 24576;  // instrumental bins of one block's histo
 constexpr int INSTR_BIN_BITS = 15;     // bin field of an instrumental entry key
 constexpr int INSTR_SMEM_BUDGET = 220 * 1024;  // dynamic shared memory of the instr kernel
 
-// One tile buffer of the instrumental kernel for ct_rows rows: keys (4 B) and
-// coefficients (8 B pair / 4 B FP32) of 6 entries per row and u of the tile
-// as pairs (8 B per row). Every part is a multiple of 16 bytes for ct_rows >= 64.
-__host__ __device__ constexpr int64_t instr_tile_bytes(int64_t ct_rows, bool f32) {
-  return 6 * ct_rows * 4 + 6 * ct_rows * (f32 ? 4 : 8) + ct_rows * 8;
+// One tile buffer of the instrumental kernel: keys (4 B) and coefficients
+// (8 B pair / 4 B FP32) of at most max_ent entries and u of the tile's
+// ct_rows rows (8 B each), every part rounded up to 16 bytes.
+__host__ __device__ constexpr int64_t instr_keys_bytes(int64_t max_ent) {
+  return (max_ent * 4 + 15) & ~15LL;
+}
+__host__ __device__ constexpr int64_t instr_vals_bytes(int64_t max_ent, bool f32) {
+  return (max_ent * (f32 ? 4 : 8) + 15) & ~15LL;
+}
+__host__ __device__ constexpr int64_t instr_tile_bytes(int64_t ct_rows, int64_t max_ent,
+                                                       bool f32) {
+  return instr_keys_bytes(max_ent) + instr_vals_bytes(max_ent, f32) + ct_rows * 8;
 }
 // Shared memory of the instrumental kernel: nbuf tile buffers (with two, the
 // next tile streams in while the current one is processed) and the float-pair
-// histogram.
-__host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t n_instr,
-                                                       bool f32, int nbuf) {
-  return nbuf * instr_tile_bytes(ct_rows, f32) + n_instr * 8;
+// histogram of one group of hist_bins columns.
+__host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t max_ent,
+                                                       int64_t hist_bins, bool f32, int nbuf) {
+  return nbuf * instr_tile_bytes(ct_rows, max_ent, f32) + hist_bins * 8;
 }
 // Two blocks of the instrumental kernel share an SM when each fits this much.
 constexpr int INSTR_SMEM_HALF = 112 * 1024;
@@ -182,6 +189,11 @@ __device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Hint: start moving bytes [src, src + bytes) from DRAM into L2 (no
+// completion to wait for; 16-byte aligned address, size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -221,14 +233,18 @@ struct Layout {
   // instrumental entries of each tile of ct_rows rows, in rounds of distinct bins
   int64_t n_ctiles;
   int32_t ct_rows;                      // power of two in [64, 2048]
+  int32_t n_bgroups;                    // instrumental columns split into groups of
+  int32_t bgroup_bins;                  // bgroup_bins; a block owns one group's histogram
+  int32_t ct_max_ent;                   // most entries of one (tile, group) segment
   int32_t ct_bufs;                      // tile buffers per block (2: double-buffered)
   int32_t ct_per_sm;                    // blocks per SM: 2 (256 threads, 1 buffer) or
                                         // 1 (512 threads, 2 buffers)
-  const int32_t* ct_round;              // [n_ctiles + 1] first round of each tile
+  const int32_t* ct_round;              // [n_ctiles * n_bgroups + 1] first round of each
+                                        // (tile, group) segment, tile-major
   const int64_t* round_entry;           // [n_rounds + 1] first entry of each round
-  const float2* ient_ff;                // [6 n_rows] coefficient (pair)
-  const float* ient_f32;                // [6 n_rows] coefficient (FP32 copy) or null
-  const uint32_t* ient_key;             // [6 n_rows] (row in tile << 15) | bin
+  const float2* ient_ff;                // coefficient (pair) of each entry; every segment
+  const float* ient_f32;                // starts at a multiple of 4 entries (padding
+  const uint32_t* ient_key;             // between); key (row in tile << 15) | column
   int* err;                             // device error word (GSR_E_TIMEOUT)
 };
 

@@ -39,10 +39,14 @@ constexpr int WS = NH + 8;           // padded bf16 row stride of the smem weigh
 // n_j is the number of rows with a coefficient slot in column j.
 // ---------------------------------------------------------------------------
 __global__ void k_instr_count(Layout L, int* __restrict__ cnt) {
-  const int64_t n = 6 * L.n_rows;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(cnt + (L.ient_key[e] & ((1u << INSTR_BIN_BITS) - 1)), 1);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned short* ins =
+        reinterpret_cast<const unsigned short*>(L.rec_ff + (r >> 6) * Rec<false>::BYTES +
+                                                Rec<false>::INSTR_I) + (r & 63);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) atomicAdd(cnt + ins[k * 64], 1);
+  }
 }
 
 __global__ void k_features(Layout L, const double* __restrict__ colnorm,
@@ -527,8 +531,7 @@ extern "C" int gsr_column_features(gsr_system* s, float* feats, void* stream) {
     if (cudaMemsetAsync(s->instr_count, 0, L.n_instr * sizeof(int), st) != cudaSuccess)
       return GSR_E_CUDA;
     if (L.n_rows > 0)
-      k_instr_count<<<grid_for(6 * L.n_rows, 256, s->num_sms * 8), 256, 0, st>>>(L,
-                                                                                 s->instr_count);
+      k_instr_count<<<grid_for(L.n_rows, 256, s->num_sms * 8), 256, 0, st>>>(L, s->instr_count);
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
   const int64_t nq = 3 * L.n_knots + L.n_instr;

@@ -24,6 +24,8 @@ SHAPES = [
     dict(n_stars=3000, obs=30, poisson=True, n_knots=200, n_instr=64, n_glob=1, seed=4),
     dict(n_stars=400, obs=1, poisson=False, n_knots=9, n_instr=7, n_glob=1, seed=5),
     dict(n_stars=5, obs=3000, poisson=False, n_knots=5000, n_instr=20000, n_glob=1, seed=6),
+    # the most instrumental columns (split into two column groups), many tiles
+    dict(n_stars=20000, obs=30, poisson=True, n_knots=3000, n_instr=24576, n_glob=1, seed=7),
 ]
 
 

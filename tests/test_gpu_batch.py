@@ -10,7 +10,8 @@ import torch
 
 import oracle
 from paper_2503_22863_b300 import synth
-from gpu_util import APROD_TOL, LSQR_TOL, aprod1_ref, aprod2_ref, scaled_err, to_dev, to_host
+from gpu_util import (APROD_TOL, LSQR_TOL, abs_system, aprod1_ref, aprod2_ref, scaled_err, to_dev,
+                      to_host)
 
 pytestmark = pytest.mark.gpu
 
@@ -140,3 +141,33 @@ def test_batched_error_history(gsr, tiny_batch):
     eh = r["err_hist"]
     assert eh.shape == (30, B.shape[1])
     assert (eh[-1] < 1e-6).all() and (eh[0] > eh[-1]).all()
+
+
+def test_batched_aprod_medium_k32_sampled_columns(gsr):
+    """The 30M-row workload with k = 32 right-hand sides (the benchmark's batched
+    configuration): three whole columns of each product against the oracle."""
+    sys = synth.make_config("medium")
+    k = 32
+    rng = np.random.default_rng(2532)
+    with gsr.System(sys) as S:
+        X = rng.standard_normal((S.n_unk, k))
+        Y = torch.zeros((S.n_rows, k), dtype=torch.float64, device="cuda")
+        S.aprod1_batch(to_dev(X), Y)
+        cols = (0, 17, k - 1)
+        Yg = {j: to_host(Y[:, j].contiguous()) for j in cols}
+        del Y
+        U = rng.standard_normal((S.n_rows, k))
+        Xo = torch.zeros((S.n_unk, k), dtype=torch.float64, device="cuda")
+        S.aprod2_batch(to_dev(U), Xo)
+        Xg = {j: to_host(Xo[:, j].contiguous()) for j in cols}
+    asys = abs_system(sys)
+    for j in cols:
+        xj, uj = np.ascontiguousarray(X[:, j]), np.ascontiguousarray(U[:, j])
+        ref, scale = np.zeros(sys["n_rows"]), np.zeros(sys["n_rows"])
+        oracle.aprod1(sys, xj, ref)
+        oracle.aprod1(asys, np.abs(xj), scale)
+        assert scaled_err(Yg[j], ref, scale) <= APROD_TOL, ("aprod1", j)
+        ref2, scale2 = np.zeros(S.n_unk), np.zeros(S.n_unk)
+        oracle.aprod2(sys, uj, ref2)
+        oracle.aprod2(asys, np.abs(uj), scale2)
+        assert scaled_err(Xg[j], ref2, scale2) <= APROD_TOL, ("aprod2", j)
