@@ -97,3 +97,37 @@ def test_create_rejects_bad_inputs_on_host(gsr):
     s0["vals"][:, 23] = np.inf
     s0["vals"][0, 0] = np.nan
     assert _create(gsr, s0) == 4
+
+
+def test_learned_entry_points_validate_arguments(gsr):
+    """The MLP / feature entry points reject bad arguments before touching a device."""
+    lib = gsr.lib
+    p = ctypes.c_void_p(8)  # never dereferenced: validation fails first
+    E_ARG = 1
+    assert lib.gsr_mlp_forward(p, -1, p, p, p, None) == E_ARG
+    assert lib.gsr_mlp_forward(None, 5, p, p, p, None) == E_ARG
+    assert lib.gsr_mlp_forward(None, 0, None, None, None, None) == 0  # nothing to do
+    assert lib.gsr_mlp_grad(p, p, 0, p, p, p, p, None, None) == E_ARG
+    assert lib.gsr_mlp_grad(p, None, 10, p, p, p, p, None, None) == E_ARG
+    assert lib.gsr_mlp_adam(p, p, p, p, 0, ctypes.c_float(1e-3), ctypes.c_float(0.9),
+                            ctypes.c_float(0.999), ctypes.c_float(1e-8), None) == E_ARG
+    assert lib.gsr_mlp_adam(p, p, p, p, 1, ctypes.c_float(0.0), ctypes.c_float(0.9),
+                            ctypes.c_float(0.999), ctypes.c_float(1e-8), None) == E_ARG
+    assert lib.gsr_mlp_adam(p, p, p, p, 1, ctypes.c_float(1e-3), ctypes.c_float(1.0),
+                            ctypes.c_float(0.999), ctypes.c_float(1e-8), None) == E_ARG
+    assert lib.gsr_feature_moments(p, -3, p, None) == E_ARG
+    assert lib.gsr_feature_moments(None, 0, p, None) == 0
+    assert lib.gsr_column_features(None, p, None) == E_ARG
+    assert lib.gsr_learned_scaling(None, None, ctypes.c_float(3.0), p, None) == E_ARG
+    assert lib.gsr_n_learned_cols(None) == 0
+
+
+def test_batch_entry_points_validate_arguments(gsr):
+    lib = gsr.lib
+    p = ctypes.c_void_p(8)
+    E_ARG = 1
+    for k in (0, 33):
+        assert lib.gsr_aprod1_batch(None, k, p, p, None) == E_ARG
+        assert lib.gsr_aprod2_batch(None, k, p, p, None) == E_ARG
+    t = ctypes.c_int()
+    assert lib.gsr_batch_tuning(None, ctypes.byref(t), ctypes.byref(t)) == E_ARG
