@@ -22,6 +22,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,7 +94,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+        self.path = os.path.join(tempfile.gettempdir(), "gsr_bench_clocks_%d_%d.csv" % (
+            gpu_index, os.getpid()))
 
     def start(self):
         try:

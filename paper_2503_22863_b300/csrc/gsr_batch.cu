@@ -56,12 +56,15 @@ __device__ __forceinline__ ff ldf(const float2* p) {
 
 // Per-right-hand-side deterministic grid reduction of NV values per lane:
 // lanes of a block with the same j = threadIdx.x % KP are summed, blocks store
-// part[(block*NV + v)*KP + j], and the last block adds them in block order
-// into tot[v*32 + j] (shared, visible to the whole last block on return true).
+// part[(block*NV + v)*KP + j], and the last block adds them into tot[v*32 + j]
+// (shared, visible to the whole last block on return true): thread group q of
+// blockDim/KP groups sums blocks q, q + groups, ... in order, and the group
+// sums are added in group order (a fixed order, independent of timing).
 // Blocks of at most 256 threads.
 template <int KP, int NV>
 __device__ bool grid_sum_kv(const double* v, double* part, unsigned int* counter, double* tot) {
   __shared__ double sh[NV][8][32];
+  __shared__ double gs[NV][256];
   __shared__ int is_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -86,13 +89,24 @@ __device__ bool grid_sum_kv(const double* v, double* part, unsigned int* counter
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  if (threadIdx.x < KP) {
+  {
+    const int groups = (int)blockDim.x / KP, q = (int)threadIdx.x / KP,
+              j = (int)threadIdx.x % KP;
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       double x = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b)
-        x += __ldcg(part + ((size_t)b * NV + a) * KP + threadIdx.x);
-      tot[a * 32 + threadIdx.x] = x;
+      for (unsigned int b = q; b < gridDim.x; b += groups)
+        x += __ldcg(part + ((size_t)b * NV + a) * KP + j);
+      gs[a][threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < KP) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        double x = 0.0;
+        for (int g = 0; g < groups; ++g) x += gs[a][g * KP + threadIdx.x];
+        tot[a * 32 + threadIdx.x] = x;
+      }
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
@@ -246,6 +260,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
 // across streams and the 4-knot window per axis advances as in the single form.
 // ---------------------------------------------------------------------------
 constexpr int ATT_B_SPLIT = 2;  // warps per knot range of the single-vector partition
+constexpr int VEC_U = 4;        // elements per thread per step of the vector kernels
 
 template <int KP>
 __global__ void __launch_bounds__(256, 2) k_aprod2_att_b(Layout L, const float2* __restrict__ Yk,
@@ -551,17 +566,31 @@ __global__ void __launch_bounds__(256) k_vec_a_b(int64_t n, const float2* __rest
   const bool frozen = sc[B_DONE * KP + j] != 0.0;
   ff s2f = ff_zero();
   if (!frozen) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      const float2 dj = d[e / KP];
-      ff t = ff_mul(ff_norm(ff_mul(ff{dj.x, dj.y}, ff_from_double(Z[e]))), ib);
-      if (!first) {
-        const float2 ve = V[e];
-        t = ff_add(t, ff_mul(nbeta, ff{ve.x, ve.y}));
+    // VEC_U elements per thread per step, all loads issued first (latency)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < n * KP;
+         e0 += VEC_U * stride) {
+      float2 dd[VEC_U], vv[VEC_U];
+      double zz[VEC_U];
+#pragma unroll
+      for (int u = 0; u < VEC_U; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < n * KP) {
+          dd[u] = d[e / KP];
+          zz[u] = Z[e];
+          if (!first) vv[u] = V[e];
+        }
       }
-      t = ff_norm(t);
-      V[e] = make_float2(t.h, t.l);
-      s2f = ff_add(s2f, ff_mul(t, t));
+#pragma unroll
+      for (int u = 0; u < VEC_U; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e >= n * KP) continue;
+        ff t = ff_mul(ff_norm(ff_mul(ff{dd[u].x, dd[u].y}, ff_from_double(zz[u]))), ib);
+        if (!first) t = ff_add(t, ff_mul(nbeta, ff{vv[u].x, vv[u].y}));
+        t = ff_norm(t);
+        V[e] = make_float2(t.h, t.l);
+        s2f = ff_add(s2f, ff_mul(t, t));
+      }
     }
   }
   const double s2 = ff_to_double(s2f);
@@ -624,42 +653,61 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
   const ff t2 = ff_from_double(first ? 0.0 : sc[B_T2 * KP + j]);
   ff dk2f = ff_zero(), x2f = ff_zero();  // ||d_k||^2, ||x||^2
   double e2 = 0.0;                       // ||x - x_ref||^2
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const float2 djf = d[e / KP];
-    const ff dj = ff{djf.x, djf.y};
-    ff xv = ff_zero();
-    if (frozen) {
-      Vff[e] = make_float2(0.f, 0.f);
-      if (!first) {
-        const float2 xf = XZ[e];
-        xv = ff_norm(ff_mul(dj, ff{xf.x, xf.y}));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < n * KP;
+       e0 += VEC_U * stride) {
+    float2 dv[VEC_U], vv[VEC_U], wv[VEC_U], xv_[VEC_U];
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < n * KP) {
+        dv[u] = d[e / KP];
+        if (!frozen) vv[u] = V[e];
+        if (!first) {
+          if (!frozen) wv[u] = W[e];
+          xv_[u] = XZ[e];
+        }
       }
-    } else {
-      const float2 vf = V[e];
-      const ff vn = ff_norm(ff_mul(ff{vf.x, vf.y}, ia));
-      if (first) {
-        W[e] = make_float2(vn.h, vn.l);
-        XZ[e] = make_float2(0.f, 0.f);
-      } else {
-        const float2 wf = W[e], xf = XZ[e];
-        const ff wj = ff{wf.x, wf.y};
-        const ff dk = ff_mul(wj, irho);
-        dk2f = ff_add(dk2f, ff_mul(dk, dk));
-        const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
-        XZ[e] = make_float2(xn.h, xn.l);
-        const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
-        W[e] = make_float2(wn.h, wn.l);
-        xv = ff_norm(ff_mul(dj, xn));
-      }
-      V[e] = make_float2(vn.h, vn.l);
-      const ff f = ff_norm(ff_mul(dj, vn));
-      Vff[e] = make_float2(f.h, f.l);
     }
-    x2f = ff_add(x2f, ff_mul(xv, xv));
-    if (xref) {
-      const double ex = ff_to_double(xv) - xref[e];
-      e2 = __fma_rn(ex, ex, e2);
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e >= n * KP) continue;
+      const float2 djf = dv[u];
+      const ff dj = ff{djf.x, djf.y};
+      ff xv = ff_zero();
+      if (frozen) {
+        Vff[e] = make_float2(0.f, 0.f);
+        if (!first) {
+          const float2 xf = xv_[u];
+          xv = ff_norm(ff_mul(dj, ff{xf.x, xf.y}));
+        }
+      } else {
+        const float2 vf = vv[u];
+        const ff vn = ff_norm(ff_mul(ff{vf.x, vf.y}, ia));
+        if (first) {
+          W[e] = make_float2(vn.h, vn.l);
+          XZ[e] = make_float2(0.f, 0.f);
+        } else {
+          const float2 wf = wv[u], xf = xv_[u];
+          const ff wj = ff{wf.x, wf.y};
+          const ff dk = ff_mul(wj, irho);
+          dk2f = ff_add(dk2f, ff_mul(dk, dk));
+          const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
+          XZ[e] = make_float2(xn.h, xn.l);
+          const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
+          W[e] = make_float2(wn.h, wn.l);
+          xv = ff_norm(ff_mul(dj, xn));
+        }
+        V[e] = make_float2(vn.h, vn.l);
+        const ff f = ff_norm(ff_mul(dj, vn));
+        Vff[e] = make_float2(f.h, f.l);
+      }
+      x2f = ff_add(x2f, ff_mul(xv, xv));
+      if (xref) {
+        const double ex = ff_to_double(xv) - xref[e];
+        e2 = __fma_rn(ex, ex, e2);
+      }
     }
   }
   double acc[3] = {ff_to_double(dk2f), ff_to_double(x2f), e2};

@@ -31,6 +31,7 @@ enum Scal {
 };
 
 constexpr int RED_BLOCKS = 148 * 8;  // grid of the vector kernels
+constexpr int VEC_U = 4;             // elements per thread per step of the vector kernels
 
 __device__ __forceinline__ double block_sum3(double& a, double& b, double& c, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -118,17 +119,31 @@ __global__ void k_vec_a(int64_t n, const float2* __restrict__ d, const double* _
   const double beta = sqrt(scal[S_UNORM2]);
   const ff ib = ff_from_double(beta > 0.0 ? 1.0 / beta : 0.0), nbeta = ff_from_double(-beta);
   ff s2f = ff_zero();
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const float2 dj = d[j];
-    ff t = ff_mul(ff_norm(ff_mul(ff{dj.x, dj.y}, ff_from_double(z[j]))), ib);
-    if (!first) {
-      const float2 vj = v[j];
-      t = ff_add(t, ff_mul(nbeta, ff{vj.x, vj.y}));
+  // VEC_U elements per thread per step, all loads issued first (latency)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < n;
+       j0 += VEC_U * stride) {
+    float2 dd[VEC_U], vv[VEC_U];
+    double zz[VEC_U];
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t j = j0 + u * stride;
+      if (j < n) {
+        dd[u] = d[j];
+        zz[u] = z[j];
+        if (!first) vv[u] = v[j];
+      }
     }
-    t = ff_norm(t);
-    v[j] = make_float2(t.h, t.l);
-    s2f = ff_add(s2f, ff_mul(t, t));
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t j = j0 + u * stride;
+      if (j >= n) continue;
+      ff t = ff_mul(ff_norm(ff_mul(ff{dd[u].x, dd[u].y}, ff_from_double(zz[u]))), ib);
+      if (!first) t = ff_add(t, ff_mul(nbeta, ff{vv[u].x, vv[u].y}));
+      t = ff_norm(t);
+      v[j] = make_float2(t.h, t.l);
+      s2f = ff_add(s2f, ff_mul(t, t));
+    }
   }
   double s2 = ff_to_double(s2f), z0 = 0.0, z1 = 0.0;
   if (!grid_sum3(s2, z0, z1, part, counter) || threadIdx.x != 0) return;
@@ -186,36 +201,55 @@ __global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restr
   const ff t2 = ff_from_double(first ? 0.0 : scal[S_T2]);
   ff dk2f = ff_zero(), x2f = ff_zero();
   double e2 = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const float2 vj = v[j], djf = d[j];
-    const ff dj = ff{djf.x, djf.y};
-    const ff vn = ff_norm(ff_mul(ff{vj.x, vj.y}, ia));
-    ff xv = ff_zero();
-    if (first) {
-      w[j] = make_float2(vn.h, vn.l);
-      xz[j] = make_float2(0.f, 0.f);
-    } else {
-      const float2 wf = w[j], xf = xz[j];
-      const ff wj = ff{wf.x, wf.y};
-      const ff dk = ff_mul(wj, irho);
-      const ff dd = ff_mul(dk, dk);
-      dk2f = ff_add(dk2f, dd);
-      if (var) var[j] += ff_to_double(dd);
-      const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
-      xz[j] = make_float2(xn.h, xn.l);
-      const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
-      w[j] = make_float2(wn.h, wn.l);
-      xv = ff_norm(ff_mul(dj, xn));
-      x2f = ff_add(x2f, ff_mul(xv, xv));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < n;
+       j0 += VEC_U * stride) {
+    float2 vv[VEC_U], dv[VEC_U], wv[VEC_U], xv_[VEC_U];
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t j = j0 + u * stride;
+      if (j < n) {
+        vv[u] = v[j];
+        dv[u] = d[j];
+        if (!first) {
+          wv[u] = w[j];
+          xv_[u] = xz[j];
+        }
+      }
     }
-    v[j] = make_float2(vn.h, vn.l);
-    const ff f = ff_norm(ff_mul(dj, vn));
-    v_ff[j] = make_float2(f.h, f.l);
-    if (x_ref) {
-      const double xd = ff_to_double(xv);
-      const double e = (x_off ? xd + x_off[j] : xd) - x_ref[j];
-      e2 = __fma_rn(e, e, e2);
+#pragma unroll
+    for (int u = 0; u < VEC_U; ++u) {
+      const int64_t j = j0 + u * stride;
+      if (j >= n) continue;
+      const float2 vj = vv[u], djf = dv[u];
+      const ff dj = ff{djf.x, djf.y};
+      const ff vn = ff_norm(ff_mul(ff{vj.x, vj.y}, ia));
+      ff xv = ff_zero();
+      if (first) {
+        w[j] = make_float2(vn.h, vn.l);
+        xz[j] = make_float2(0.f, 0.f);
+      } else {
+        const float2 wf = wv[u], xf = xv_[u];
+        const ff wj = ff{wf.x, wf.y};
+        const ff dk = ff_mul(wj, irho);
+        const ff dd = ff_mul(dk, dk);
+        dk2f = ff_add(dk2f, dd);
+        if (var) var[j] += ff_to_double(dd);
+        const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
+        xz[j] = make_float2(xn.h, xn.l);
+        const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
+        w[j] = make_float2(wn.h, wn.l);
+        xv = ff_norm(ff_mul(dj, xn));
+        x2f = ff_add(x2f, ff_mul(xv, xv));
+      }
+      v[j] = make_float2(vn.h, vn.l);
+      const ff f = ff_norm(ff_mul(dj, vn));
+      v_ff[j] = make_float2(f.h, f.l);
+      if (x_ref) {
+        const double xd = ff_to_double(xv);
+        const double e = (x_off ? xd + x_off[j] : xd) - x_ref[j];
+        e2 = __fma_rn(e, e, e2);
+      }
     }
   }
   double dk2 = ff_to_double(dk2f), x2 = ff_to_double(x2f);

@@ -32,7 +32,7 @@ def aprod2_ref(sys, y, x0):
 
 
 def scaled_err(got, ref, scale):
-    """max_i |got - ref| / max_i scale_i (the benchmark spec's aprod measure)."""
+    """max_i |got - ref| / max_i scale_i (the aprod accuracy measure)."""
     den = float(np.max(scale)) if scale.size else 1.0
     if den == 0.0:
         den = 1.0

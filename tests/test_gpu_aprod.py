@@ -3,8 +3,8 @@
 Element by element on seeded systems: the tiny 100,000-row workload, ragged
 small shapes (partial last tile, single star, minimum knots and instrumental
 columns, no global column, stars spanning lanes, tiles and warp ranges), and
-the full 30M-row workload in the bench's launch configuration. The bar is the
-the benchmark spec's: max |gpu - oracle| / max (|A||x|) <= 1e-12 (aprod 1) and the
+the full 30M-row workload in the bench's launch configuration. The bar:
+max |gpu - oracle| / max (|A||x|) <= 1e-12 (aprod 1) and the
 same with |A|^T|y| (aprod 2)."""
 import numpy as np
 import pytest
