@@ -859,15 +859,11 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
   const Layout& L = sys->L;
   if (L.n_rows <= 0) return GSR_OK;
   const bool f32 = which_values == GSR_VALUES_F32;
-  // attitude part on the side stream, concurrent with the star-ordered parts
+  // The latency-bound instrumental part is launched first on the caller's
+  // stream; the attitude and then the astrometric part, which stream at full
+  // bandwidth, run beside it on the side stream.
   if (cudaEventRecord(sys->ev_fork, st) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(sys->side, sys->ev_fork, 0) != cudaSuccess) return GSR_E_CUDA;
-  const int att_blocks = (L.n_att_warps + 7) / 8;
-  if (att_blocks > 0) {
-    if (f32) k_aprod2_att<true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
-    else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
-    if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
-  }
   // G column groups, each over tile streams of num_sms * per_sm / G blocks
   const int64_t per_group = std::max<int64_t>(
       1, std::min<int64_t>((int64_t)sys->num_sms * L.ct_per_sm / L.n_bgroups, L.n_ctiles));
@@ -884,9 +880,15 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
     }
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
+  const int att_blocks = (L.n_att_warps + 7) / 8;
+  if (att_blocks > 0) {
+    if (f32) k_aprod2_att<true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  }
   const int ab = (int)std::min<int64_t>((int64_t)sys->num_sms * 8, ((L.n_recs + 1) / 2 + 7) / 8);
-  if (f32) k_aprod2_astro<true><<<ab, 256, 0, st>>>(L, y, x, stop);
-  else k_aprod2_astro<false><<<ab, 256, 0, st>>>(L, y, x, stop);
+  if (f32) k_aprod2_astro<true><<<ab, 256, 0, sys->side>>>(L, y, x, stop);
+  else k_aprod2_astro<false><<<ab, 256, 0, sys->side>>>(L, y, x, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   if (cudaEventRecord(sys->ev_join, sys->side) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(st, sys->ev_join, 0) != cudaSuccess) return GSR_E_CUDA;
