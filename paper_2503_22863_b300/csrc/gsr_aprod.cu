@@ -673,7 +673,10 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) win[a][j] = ff_zero();
   const int64_t K = L.n_knots;
-  constexpr int U = 4;  // positions per lane per step
+  // positions per lane per step: 2 keeps the kernel at ~128 registers, so a block
+  // fits beside the instrumental kernel's block on every SM (measured better
+  // than 4 positions at ~180 registers: 30M rows 1.60 -> 1.56 ms for aprod 2)
+  constexpr int U = 2;
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
     ff acc[12];
