@@ -147,6 +147,18 @@ def test_aprod_f32_storage(gsr, values):
     assert e1 <= APROD_TOL and e2 <= APROD_TOL, (e1, e2)
 
 
+@pytest.mark.parametrize("values", ["f64", "f32"])
+@pytest.mark.parametrize("n_instr", [6145, 10000, 20000, 24576])
+def test_aprod_instr_beyond_shared_memory(gsr, values, n_instr):
+    # more instrumental unknowns than aprod 1 stages in shared memory beside its
+    # record buffers (6,144): they are gathered through L1/L2 instead; one past
+    # the limit up to the maximum, both value precisions, ragged last record
+    sys = synth.make_system(n_stars=1500, n_knots=200, n_instr=n_instr, n_glob=1, obs=21,
+                            poisson=True, seed=n_instr)
+    e1, e2 = _check_pair(gsr, sys, storage="f32+f64", values=values, rng_seed=5)
+    assert e1 <= APROD_TOL and e2 <= APROD_TOL, (e1, e2)
+
+
 def test_aprod_parity_medium_full_size(gsr):
     """The 30M-row workload (the benchmark's), every element against the oracle."""
     sys = synth.make_config("medium")

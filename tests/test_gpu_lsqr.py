@@ -79,6 +79,20 @@ def test_lsqr_planted_solution(gsr):
     assert np.max(np.abs(to_host(r["x"]) - 1.0)) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("n_instr", [10000, 20000])
+def test_lsqr_many_instrumental_columns(gsr, precision, n_instr):
+    # more instrumental unknowns than aprod 1 stages in shared memory: the LSQR
+    # form gathers them through L1/L2 (FP64 pairs and, mixed, FP32 values)
+    sys = synth.make_system(n_stars=2500, n_knots=150, n_instr=n_instr, n_glob=1, obs=60,
+                            poisson=True, seed=23)
+    b = rhs(sys)
+    ref = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
+    with gsr.System(sys, storage="f32+f64" if precision == "mixed" else "f64") as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, precision=precision, itnlim=5000)
+    assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
+
+
 def test_lsqr_zero_rhs_and_itnlim(gsr):
     sys = synth.make_system(n_stars=100, n_knots=20, n_instr=10, n_glob=1, obs=12, seed=23)
     with gsr.System(sys) as S:
