@@ -514,14 +514,35 @@ __global__ void __launch_bounds__(256) k_aprod2_astro(Layout L, const float2* __
 
 // ---------------------------------------------------------------------------
 // aprod 2, instrumental part. One block per tile of ct_rows rows (grid-stride).
-// The tile's entries (coefficient, row, bin) are sorted at setup into rounds
-// in which every bin appears at most once; they are TMA-copied into shared
-// memory together with the tile's u (two buffers: the block's next tile
-// streams in while it works on the current one), and each round adds its
-// products into the block's float-pair histogram with plain read-modify-write
-// (distinct bins: no conflicts), a barrier separating rounds. The histogram
-// is added into x at the end.
+// The tile's entries (coefficient, row, bin) of one column group are
+// TMA-copied into shared memory together with the tile's u (two buffers: the
+// block's next tile streams in while it works on the current one); each
+// product is added into the block's float-pair histogram of the group's
+// columns by a 64-bit compare-and-swap of the pair (lock-free: some thread
+// wins every round of a conflict, and retries are bounded), so a tile needs no
+// barrier between its entries. (Setup orders a tile's entries in rounds of
+// distinct bins, so neighbouring threads rarely meet on one bin.) The
+// histogram is added into x at the end.
 // ---------------------------------------------------------------------------
+constexpr int IU = 4;              // entries per thread per pass
+constexpr int CAS_LIMIT = 1 << 16; // compare-and-swap attempts before giving up
+
+// hist += p by compare-and-swap on the (hi, lo) pair; false if it gave up
+__device__ __forceinline__ bool hist_add(float2* hist, ff p) {
+  unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
+  unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(h);
+  for (int i = 0; i < CAS_LIMIT; ++i) {
+    const ff cur{__uint_as_float((unsigned)old), __uint_as_float((unsigned)(old >> 32))};
+    const ff nh = ff_add(cur, p);
+    const unsigned long long nv = (unsigned long long)__float_as_uint(nh.h) |
+                                  ((unsigned long long)__float_as_uint(nh.l) << 32);
+    const unsigned long long prev = atomicCAS(h, old, nv);
+    if (prev == old) return true;
+    old = prev;
+  }
+  return false;
+}
+
 template <bool F32, int NBUF, int NTH>
 __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     k_aprod2_instr(Layout L, const float2* __restrict__ y, double* __restrict__ x,
@@ -569,7 +590,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     }
   };
   uint32_t parity = 0u, pending = 0u;  // bit q: phase / copy in flight of buffer q
-  bool ok = true;
+  bool ok = true, cas_ok = true;
   int b = 0;
   const int64_t t0 = blockIdx.x / G;
   if (NBUF == 2 && t0 < L.n_ctiles) {
@@ -603,29 +624,40 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     const unsigned char* vals = smem + b * TB + KB;
     const float2* us = reinterpret_cast<const float2*>(smem + b * TB + KB + VBB);
     const int64_t c = ct * G + g;
-    const int k0 = L.ct_round[c], k1 = L.ct_round[c + 1] - 1;  // the last slot ends the segment
-    const int64_t e0 = L.round_entry[k0];
-    for (int k = k0; k < k1; ++k) {
-      const int a = (int)(L.round_entry[k] - e0), bb = (int)(L.round_entry[k + 1] - e0);
-      for (int e = a + threadIdx.x; e < bb; e += blockDim.x) {
-        const uint32_t key = keys[e];
-        const int row = (int)(key >> INSTR_BIN_BITS);
-        const int bin = (int)(key & ((1u << INSTR_BIN_BITS) - 1)) - bin_lo;
-        const float2 uu = us[row];
-        ff p;
-        if constexpr (F32) {
-          p = f_mul(reinterpret_cast<const float*>(vals)[e], ff{uu.x, uu.y});
-        } else {
-          const float2 vv = reinterpret_cast<const float2*>(vals)[e];
-          p = ff_mul(ff{vv.x, vv.y}, ff{uu.x, uu.y});
+    // the segment's entries [e0, e1): the last round slot is its exact end
+    const int64_t e0 = L.round_entry[L.ct_round[c]];
+    const int ne = (int)(L.round_entry[L.ct_round[c + 1] - 1] - e0);
+    for (int e = threadIdx.x; e < ne; e += NTH * IU) {
+      // IU entries per thread: their shared-memory reads issue together, then
+      // each product goes into the histogram by compare-and-swap
+      ff p[IU];
+      int bin[IU];
+#pragma unroll
+      for (int j = 0; j < IU; ++j) {
+        const int ej = e + j * NTH;
+        bin[j] = -1;
+        p[j] = ff_zero();
+        if (ej < ne) {
+          const uint32_t key = keys[ej];
+          const int row = (int)(key >> INSTR_BIN_BITS);
+          bin[j] = (int)(key & ((1u << INSTR_BIN_BITS) - 1)) - bin_lo;
+          const float2 uu = us[row];
+          if constexpr (F32) {
+            p[j] = f_mul(reinterpret_cast<const float*>(vals)[ej], ff{uu.x, uu.y});
+          } else {
+            const float2 vv = reinterpret_cast<const float2*>(vals)[ej];
+            p[j] = ff_mul(ff{vv.x, vv.y}, ff{uu.x, uu.y});
+          }
         }
-        const float2 h = hist[bin];
-        const ff nh = ff_add(ff{h.x, h.y}, p);
-        hist[bin] = make_float2(nh.h, nh.l);
       }
-      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < IU; ++j)
+        if (bin[j] >= 0 && !hist_add(hist + bin[j], p[j])) cas_ok = false;
     }
+    // every thread is done with buffer b before a copy into it is issued
+    __syncthreads();
   }
+  if (!cas_ok) atomicExch(L.err, GSR_E_TIMEOUT);
   if (!ok) {
     // let the copies still in flight land before the block exits (bounded)
     for (int q = 0; q < NBUF; ++q)
