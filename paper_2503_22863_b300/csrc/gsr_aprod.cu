@@ -569,12 +569,16 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     fence_proxy_async();
   }
   __syncthreads();
-  // thread 0: start the copies of segment (tile ct, group g) into buffer b
-  auto issue = [&](int64_t ct, int b) {
+  __shared__ int seg_n_s[2];  // entries of the segment in each buffer
+  // (first entry, entries) of the segment of tile ct in this block's group
+  auto seg_of = [&](int64_t ct) {
+    return ct < L.n_ctiles ? L.iseg[ct * G + g] : make_longlong2(0, 0);
+  };
+  // thread 0: start the copies of segment sg (tile ct, group g) into buffer b
+  auto issue = [&](int64_t ct, int b, longlong2 sg) {
     unsigned char* base = smem + b * TB;
-    const int64_t c = ct * G + g;
-    const int64_t e0 = L.round_entry[L.ct_round[c]], e1 = L.round_entry[L.ct_round[c + 1] - 1];
-    const int64_t ne = e1 - e0;
+    const int64_t e0 = sg.x, ne = sg.y;
+    seg_n_s[b] = (int)ne;
     fence_proxy_async();
     // sizes rounded up to 16 bytes (segments start 16-byte aligned and the
     // entry arrays are padded); u is padded to whole tiles
@@ -593,18 +597,28 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
   bool ok = true, cas_ok = true;
   int b = 0;
   const int64_t t0 = blockIdx.x / G;
-  if (NBUF == 2 && t0 < L.n_ctiles) {
-    if (threadIdx.x == 0) issue(t0, 0);
-    pending = 1u;
+  // thread 0 loads each segment's (first entry, entries) one copy ahead of
+  // the copy that needs it, so that the load's latency stays off its path
+  longlong2 nxt = make_longlong2(0, 0);
+  if (threadIdx.x == 0) {
+    if (NBUF == 2 && t0 < L.n_ctiles) issue(t0, 0, seg_of(t0));
+    nxt = seg_of(NBUF == 2 ? t0 + T : t0);
   }
+  if (NBUF == 2 && t0 < L.n_ctiles) pending = 1u;
   for (int64_t ct = t0; ct < L.n_ctiles; ct += T, b ^= (NBUF - 1)) {
     // the buffer written here was last read by the previous tile, which ended
     // in a barrier
     if (NBUF == 1) {
-      if (threadIdx.x == 0) issue(ct, 0);
+      if (threadIdx.x == 0) {
+        issue(ct, 0, nxt);
+        nxt = seg_of(ct + T);
+      }
       pending = 1u;
     } else if (ct + T < L.n_ctiles) {
-      if (threadIdx.x == 0) issue(ct + T, b ^ 1);
+      if (threadIdx.x == 0) {
+        issue(ct + T, b ^ 1, nxt);
+        nxt = seg_of(ct + 2 * T);
+      }
       pending |= 1u << (b ^ 1);
     }
     bool got = false;
@@ -623,10 +637,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     const uint32_t* keys = reinterpret_cast<const uint32_t*>(smem + b * TB);
     const unsigned char* vals = smem + b * TB + KB;
     const float2* us = reinterpret_cast<const float2*>(smem + b * TB + KB + VBB);
-    const int64_t c = ct * G + g;
-    // the segment's entries [e0, e1): the last round slot is its exact end
-    const int64_t e0 = L.round_entry[L.ct_round[c]];
-    const int ne = (int)(L.round_entry[L.ct_round[c + 1] - 1] - e0);
+    const int ne = seg_n_s[b];
     for (int e = threadIdx.x; e < ne; e += NTH * IU) {
       // IU entries per thread: their shared-memory reads issue together, then
       // each product goes into the histogram by compare-and-swap

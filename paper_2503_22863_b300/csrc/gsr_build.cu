@@ -114,7 +114,7 @@ void free_system(gsr_system* s) {
   if (!s) return;
   destroy_batch(s);
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
-                  s->att_warp_knot, s->ct_round, s->round_entry, s->ient_ff, s->ient_f32,
+                  s->att_warp_knot, s->iseg, s->ient_ff, s->ient_f32,
                   s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
                   s->dscale, s->dscale_ff, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
                   s->S.count, s->S.x_ff, s->S.x3,
@@ -173,13 +173,11 @@ void parallel_for(int64_t n, unsigned nt, F f) {
 // groups of bpg consecutive columns), each (tile, group) segment ordered into
 // rounds in which every column occurs at most once (round = earlier
 // occurrences of the column in the tile) and by column inside a round.
-// Segments are stored tile-major, each starting at a multiple of 4 entries.
-// Segment c owns round slots [ct_round[c], ct_round[c+1]); the last slot is a
-// terminator whose round_entry is the segment's exact end (the padding after
-// a segment belongs to no round).
+// Segments are stored tile-major, each starting at a multiple of 4 entries;
+// seg[c] = (first entry, entries) of segment c (the padding after a segment
+// belongs to none).
 struct InstrRounds {
-  std::vector<int32_t> ct_round;
-  std::vector<int64_t> round_entry;
+  std::vector<longlong2> seg;
   std::vector<uint32_t> key;
   std::vector<float2> vff;
   std::vector<float> vf32;
@@ -191,35 +189,23 @@ void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* in
   const int64_t n = d.n_rows;
   const int64_t n_ct = (n + ct - 1) / ct;
   const int64_t n_seg = n_ct * G;
-  std::vector<int32_t> rounds(n_seg, 0);
   std::vector<int64_t> seg_n(n_seg, 0);
   std::vector<std::vector<int32_t>> occ(nt, std::vector<int32_t>(d.n_instr, 0));
   parallel_for(n_ct, nt, [&](int64_t t, unsigned w) {
     auto& o = occ[w];
     const int64_t a = t * ct, b = std::min<int64_t>(n, a + ct);
     for (int64_t i = a; i < b; ++i)
-      for (int k = 0; k < 6; ++k) {
-        const int bin = instr[i * 6 + k];
-        const int g = bin / bpg;
-        rounds[t * G + g] = std::max(rounds[t * G + g], ++o[bin]);
-        ++seg_n[t * G + g];
-      }
-    for (int64_t i = a; i < b; ++i)
-      for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
+      for (int k = 0; k < 6; ++k) ++seg_n[t * G + instr[i * 6 + k] / bpg];
   });
   std::vector<int64_t> seg_start(n_seg + 1, 0);
-  out.ct_round.assign(n_seg + 1, 0);
+  out.seg.resize(n_seg);
   out.max_ent = 0;
   for (int64_t c = 0; c < n_seg; ++c) {
-    out.ct_round[c + 1] = out.ct_round[c] + rounds[c] + 1;
     seg_start[c + 1] = (seg_start[c] + seg_n[c] + 3) & ~3LL;  // next segment 16-B aligned
+    out.seg[c] = make_longlong2(seg_start[c], seg_n[c]);
     out.max_ent = std::max(out.max_ent, seg_n[c]);
   }
-  const int64_t n_slots = out.ct_round[n_seg];
   const int64_t n_ent = seg_start[n_seg];
-  out.round_entry.assign(n_slots + 1, n_ent);
-  for (int64_t c = 0; c < n_seg; ++c)  // terminators: exact segment ends
-    out.round_entry[out.ct_round[c + 1] - 1] = seg_start[c] + seg_n[c];
   out.key.assign(n_ent + 4, 0u);  // +4: TMA copies are rounded up to 16 bytes
   out.vff.assign(n_ent + 4, make_float2(0.f, 0.f));
   if (want_f32) out.vf32.assign(n_ent + 4, 0.f);
@@ -239,22 +225,15 @@ void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* in
     for (int64_t i = a; i < b; ++i)
       for (int k = 0; k < 6; ++k) o[instr[i * 6 + k]] = 0;
     std::sort(order.begin(), order.end());
-    int64_t cur_g = -1, cur_r = -1, e = 0, kr = 0;
+    int64_t cur_g = -1, e = 0;
     for (uint64_t v : order) {
       const int64_t g = (int64_t)(v >> 58);
-      const int64_t rnd = (int64_t)((v >> 40) & 0x3ffff);
       const uint32_t bin = (uint32_t)((v >> 24) & 0xffff);
       const int64_t row = (int64_t)((v >> 3) & 0x1fffff);
       const int k = (int)(v & 7);
       if (g != cur_g) {
         e = seg_start[t * G + g];
-        kr = out.ct_round[t * G + g];
         cur_g = g;
-        cur_r = -1;
-      }
-      if (rnd != cur_r) {
-        out.round_entry[kr + rnd] = e;
-        cur_r = rnd;
       }
       out.key[e] = ((uint32_t)row << INSTR_BIN_BITS) | bin;
       const double x = vals[(a + row) * NSLOT + 17 + k];
@@ -325,11 +304,11 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     for (int64_t r = 0; r < n; ++r) pos[r] = (int32_t)(next[s_knot[r]]++);
   }
   // ---- instrumental tiles and column groups ----
-  // Larger tiles mean fewer, fuller rounds per entry. The columns are split
+  // Larger tiles mean fewer tile switches per entry. The columns are split
   // into the fewest groups (each block holds one group's histogram) that still
   // allow tiles of at least 1024 rows; then the largest tile wins, and between
   // equal tiles two single-buffered 256-thread blocks per SM (one block's
-  // barrier waits overlap the other's work) beat one double-buffered
+  // copy waits overlap the other's work) beat one double-buffered
   // 512-thread block. The sizes are checked against the exact segment counts.
   InstrRounds ir;
   int ct = 0, G = 1, bpg = (int)d.n_instr, ct_bufs = 2, ct_per_sm = 1;
@@ -387,7 +366,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.ct_max_ent = (int32_t)ir.max_ent;
   L.ct_bufs = ct_bufs;
   L.ct_per_sm = ct_per_sm;
-  L.n_ctiles = ((int64_t)ir.ct_round.size() - 1) / G;
+  L.n_ctiles = (int64_t)ir.seg.size() / G;
 
   L.n_att_warps = sys->num_sms * 8;  // one 8-warp block per SM (the kernel holds ~180 registers)
   std::vector<int32_t> att_warp_knot(L.n_att_warps + 1);
@@ -404,7 +383,6 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
 
   // ---- device allocations ----
   const size_t n_ent = ir.key.size();
-  const size_t n_rounds = ir.round_entry.size();
   int rc = GSR_OK;
   auto A = [&](int r) {
     if (rc == GSR_OK) rc = r;
@@ -416,8 +394,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   if (want_f32) A(dalloc(&sys->att_knot_f32, (size_t)n * 12));
   A(dalloc(&sys->knot_start, (size_t)n_buckets + 1));
   A(dalloc(&sys->att_warp_knot, (size_t)L.n_att_warps + 1));
-  A(dalloc(&sys->ct_round, ir.ct_round.size()));
-  A(dalloc(&sys->round_entry, n_rounds));
+  A(dalloc(&sys->iseg, ir.seg.size()));
   A(dalloc(&sys->ient_key, n_ent));
   A(dalloc(&sys->ient_ff, n_ent));
   if (want_f32) A(dalloc(&sys->ient_f32, n_ent));
@@ -460,9 +437,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
                     cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->att_warp_knot, att_warp_knot.data(), (size_t)(L.n_att_warps + 1) * 4,
                     cudaMemcpyHostToDevice, st));
-  C(cudaMemcpyAsync(sys->ct_round, ir.ct_round.data(), ir.ct_round.size() * 4,
-                    cudaMemcpyHostToDevice, st));
-  C(cudaMemcpyAsync(sys->round_entry, ir.round_entry.data(), n_rounds * 8,
+  C(cudaMemcpyAsync(sys->iseg, ir.seg.data(), ir.seg.size() * sizeof(longlong2),
                     cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->ient_key, ir.key.data(), n_ent * 4, cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->ient_ff, ir.vff.data(), n_ent * 8, cudaMemcpyHostToDevice, st));
@@ -477,8 +452,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.att_knot_f32 = sys->att_knot_f32;
   L.knot_start = sys->knot_start;
   L.att_warp_knot = sys->att_warp_knot;
-  L.ct_round = sys->ct_round;
-  L.round_entry = sys->round_entry;
+  L.iseg = sys->iseg;
   L.ient_ff = sys->ient_ff;
   L.ient_f32 = sys->ient_f32;
   L.ient_key = sys->ient_key;

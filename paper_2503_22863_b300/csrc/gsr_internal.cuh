@@ -239,9 +239,8 @@ struct Layout {
   int32_t ct_bufs;                      // tile buffers per block (2: double-buffered)
   int32_t ct_per_sm;                    // blocks per SM: 2 (256 threads, 1 buffer) or
                                         // 1 (512 threads, 2 buffers)
-  const int32_t* ct_round;              // [n_ctiles * n_bgroups + 1] first round of each
-                                        // (tile, group) segment, tile-major
-  const int64_t* round_entry;           // [n_rounds + 1] first entry of each round
+  const longlong2* iseg;                // [n_ctiles * n_bgroups] (first entry, entries)
+                                        // of each (tile, group) segment, tile-major
   const float2* ient_ff;                // coefficient (pair) of each entry; every segment
   const float* ient_f32;                // starts at a multiple of 4 entries (padding
   const uint32_t* ient_key;             // between); key (row in tile << 15) | column

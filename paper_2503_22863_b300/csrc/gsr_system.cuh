@@ -19,8 +19,7 @@ struct gsr_system {
   float* att_knot_f32;
   int64_t* knot_start;
   int32_t* att_warp_knot;
-  int32_t* ct_round;
-  int64_t* round_entry;
+  longlong2* iseg;
   float2* ient_ff;
   float* ient_f32;
   uint32_t* ient_key;
