@@ -366,6 +366,201 @@ __global__ void __launch_bounds__(NW * 32, 1)
 }
 
 // ---------------------------------------------------------------------------
+// aprod 1, warp-pair form: the same computation as k_aprod1 with NP pairs of
+// warps per block. The two warps of a pair share the pair's NS record buffers
+// and take one half of each record (lane l: row 32 h + l of the record); the
+// warp that finishes a buffer second refills it (a counter per buffer in
+// shared memory, acquire/release), so twice as many warps share the same
+// shared memory as in k_aprod1.
+// ---------------------------------------------------------------------------
+template <bool F32>
+__device__ __forceinline__ ff rec_val1(const unsigned char* rec, int t, int ri) {
+  if constexpr (F32) {
+    return ff{*reinterpret_cast<const float*>(rec + slot_offset<true>(t) + ri * 4), 0.0f};
+  } else {
+    const float2 v = *reinterpret_cast<const float2*>(rec + slot_offset<false>(t) + ri * 8);
+    return ff{v.x, v.y};
+  }
+}
+// old value of *c before adding 1 (shared memory, acquire-release at CTA scope)
+__device__ __forceinline__ uint32_t smem_add_acq_rel(uint32_t* c) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;"
+               : "=r"(old)
+               : "r"(smem_u32(c))
+               : "memory");
+  return old;
+}
+
+template <bool F32, bool YFF, bool X3, int NP, int NS>
+__global__ void __launch_bounds__(NP * 64, 1)
+    k_aprod1p(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
+              void* __restrict__ yv, const double* __restrict__ coef_dev, double coef_host,
+              float2* __restrict__ y_knot, double* part, unsigned int* counter, double* norm_out,
+              const double* stop, int instr_in_smem) {
+  if (stop && *stop != 0.0) return;
+  using R = Rec<F32>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[NP * NS];
+  __shared__ uint32_t done[NP * NS];  // halves finished with each buffer (mod 2)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, pr = wid >> 1, half = wid & 1;
+  unsigned char* stage0 = smem + (size_t)pr * NS * R::BYTES;
+  float2* xi_s = reinterpret_cast<float2*>(smem + (size_t)NP * NS * R::BYTES);
+  if (instr_in_smem)
+    for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) xi_s[i] = __ldg(x + L.instr_base + i);
+  const double4_32a* __restrict__ x3q = reinterpret_cast<const double4_32a*>(x3);
+  uint64_t* bar = bars + pr * NS;
+  uint32_t* dn = done + pr * NS;
+  const int64_t gp = (int64_t)blockIdx.x * NP + pr, np = (int64_t)gridDim.x * NP;
+  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
+  const double coef = coef_dev ? *coef_dev : coef_host;
+  const ff coef_ff = ff_from_double(coef);
+  const bool glob = L.n_glob == 1;
+  const ff xg = glob ? ldx(x, L.glob_col) : ff_zero();
+
+  if (half == 0 && lane == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&bar[s], 1);
+      dn[s] = 0u;
+    }
+    fence_proxy_async();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int64_t r = gp + s * np;
+      if (r < L.n_recs) {
+        mbar_expect_tx(&bar[s], R::BYTES);
+        tma_load(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < A1_PF; ++k) {
+      const int64_t rp = gp + (NS + k) * np;
+      if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
+    }
+  }
+  // the partner warp waits on barriers the first warp initialised
+  __syncthreads();
+
+  const int ri = half * 32 + lane;  // this lane's row inside a record
+  ff nrm = ff_zero();
+  double nrm_d = 0.0;
+  uint32_t parity = 0;
+  bool ok = true;
+  int s = 0;
+  for (int64_t r = gp; r < L.n_recs; r += np) {
+    const unsigned char* rec = stage0 + s * R::BYTES;
+    const int64_t row = r * REC_ROWS + ri;
+    const bool live = row < L.n_rows;
+    ff yo = ff_zero();
+    double yd = 0.0;
+    if constexpr (YFF) {
+      if (live) {
+        const float2 a = static_cast<const float2*>(yv)[row];
+        yo = ff{a.x, a.y};
+      }
+    } else {
+      if (live) yd = static_cast<const double*>(yv)[row];
+    }
+    bool got = false;
+    for (int i = 0; i < WAIT_LIMIT; ++i)
+      if (__all_sync(0xffffffffu, mbar_try_wait(&bar[s], (parity >> s) & 1u))) {
+        got = true;
+        break;
+      }
+    if (!got) {
+      if (lane == 0) atomicExch(L.err, GSR_E_TIMEOUT);
+      ok = false;
+      break;
+    }
+    parity ^= 1u << s;
+
+    const int st = reinterpret_cast<const int*>(rec + R::STAR)[ri];
+    const int sk = reinterpret_cast<const int*>(rec + R::ATT_S)[ri];
+    int ik[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      ik[k] = reinterpret_cast<const unsigned short*>(rec + R::INSTR_I + k * 128)[ri];
+    ff xv[NSLOT];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) xv[t] = ldx(x, 5 * (int64_t)st + t);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if constexpr (X3) {
+        const double4_32a q = x3q[(int64_t)sk * 3 + a];
+        xv[5 + 4 * a + 0] = ff_lo(q.x);
+        xv[5 + 4 * a + 1] = ff_lo(q.y);
+        xv[5 + 4 * a + 2] = ff_lo(q.z);
+        xv[5 + 4 * a + 3] = ff_lo(q.w);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[5 + 4 * a + i] = ldx(x, L.att_base + a * L.n_knots + sk + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (instr_in_smem) {
+        const float2 v = xi_s[ik[k]];
+        xv[17 + k] = ff{v.x, v.y};
+      } else {
+        xv[17 + k] = ldx(x, L.instr_base + ik[k]);
+      }
+    }
+    xv[23] = xg;
+    // five independent accumulation chains: astro, 3 attitude axes,
+    // instrumental (+ global), combined by a tree at the end
+    ff pa[5];
+#pragma unroll
+    for (int g = 0; g < 5; ++g) pa[g] = ff_zero();
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      if (t == 23 && !glob) continue;
+      const int g = t < 5 ? 0 : t < 9 ? 1 : t < 13 ? 2 : t < 17 ? 3 : 4;
+      pa[g] = ff_add(pa[g], val_mul<F32>(rec_val1<F32>(rec, t, ri), xv[t]));
+    }
+    const ff acc = ff_add(ff_add(ff_add(pa[0], pa[1]), ff_add(pa[2], pa[3])), pa[4]);
+    const int ps = reinterpret_cast<const int*>(rec + R::POS)[ri];
+    // every lane of this warp is done with the buffer
+    __syncwarp();
+    if (lane == 0) {
+      // the second half to finish refills it with the record NS steps ahead
+      if (smem_add_acq_rel(&dn[s]) & 1u) {
+        const int64_t rn = r + NS * np;
+        if (rn < L.n_recs) {
+          fence_proxy_async();
+          mbar_expect_tx(&bar[s], R::BYTES);
+          tma_load(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s]);
+        }
+        const int64_t rp = rn + A1_PF * np;
+        if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
+      }
+    }
+    if constexpr (YFF) {
+      const ff yn = ff_norm(ff_add(ff_mul(coef_ff, yo), acc));
+      if (live) {
+        static_cast<float2*>(yv)[row] = make_float2(yn.h, yn.l);
+        nrm = ff_add(nrm, ff_mul(yn, yn));
+        if (y_knot) y_knot[ps] = make_float2(yn.h, yn.l);
+      }
+    } else {
+      const double yn = __fma_rn(coef, yd, ff_to_double(acc));
+      if (live) {
+        static_cast<double*>(yv)[row] = yn;
+        nrm_d = __fma_rn(yn, yn, nrm_d);
+      }
+    }
+    s = (s + 1 == NS) ? 0 : s + 1;
+  }
+  if (!ok) {
+    // give copies still in flight on the pair's buffers a bounded chance to land
+    for (int q = 0; q < NS; ++q)
+      for (int i = 0; i < WAIT_LIMIT / 16; ++i)
+        if (mbar_try_wait(&bar[q], (parity >> q) & 1u)) break;
+  }
+  if (norm_out) grid_sum_store(YFF ? ff_to_double(nrm) : nrm_d, part, counter, norm_out);
+}
+
+// ---------------------------------------------------------------------------
 // aprod 2, astrometric + global part. One warp per two records (grid-stride),
 // the four rows of a lane are consecutive; per-star runs are summed in
 // registers, joined across lanes by a segmented inclusive scan and added into
@@ -780,6 +975,8 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
 constexpr int A1_NW = 6;                    // warps per aprod 1 block (one block per SM)
 constexpr int A1_NS_FF = 2, A1_NS_F32 = 3;  // record buffers per warp
 constexpr int A1_XI_SMEM_MAX = 6144;        // instrumental unknowns staged in shared memory
+// warp pairs (k_aprod1p) instead of one warp per record buffer set (k_aprod1)
+constexpr bool A1_PAIRS = true;
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSR_OK : GSR_E_CUDA; }
 
@@ -801,6 +998,18 @@ int set_kernel_attributes() {
   C(cudaFuncSetAttribute(k_aprod1<true, false, true, A1_NW, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
   C(cudaFuncSetAttribute(k_aprod1<true, false, false, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<false, true, true, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<false, false, true, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<false, false, false, A1_NW, A1_NS_FF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<true, true, true, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<true, false, true, A1_NW, A1_NS_F32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
+  C(cudaFuncSetAttribute(k_aprod1p<true, false, false, A1_NW, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
 #define GSR_INSTR_ATTR(F, B, T)                                                             \
   C(cudaFuncSetAttribute(k_aprod2_instr<F, B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -866,6 +1075,20 @@ static int launch_aprod1_t(gsr_system* sys, int which_values, const float2* x_ff
   if (need < blocks) blocks = (int)need;
   const int xi = L.n_instr <= A1_XI_SMEM_MAX ? 1 : 0;
   const int xib = xi ? (int)L.n_instr * 8 : 0;
+  if (A1_PAIRS) {
+    // A1_NW pairs of warps share A1_NW buffer sets: twice the warps of k_aprod1
+    if (which_values == GSR_VALUES_F32)
+      k_aprod1p<true, YFF, X3, A1_NW, A1_NS_F32>
+          <<<blocks, A1_NW * 64, A1_NW * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
+              L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+              norm_slot, stop, xi);
+    else
+      k_aprod1p<false, YFF, X3, A1_NW, A1_NS_FF>
+          <<<blocks, A1_NW * 64, A1_NW * A1_NS_FF * Rec<false>::BYTES + xib, st>>>(
+              L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+              norm_slot, stop, xi);
+    return cuda_status(cudaGetLastError());
+  }
   if (which_values == GSR_VALUES_F32)
     k_aprod1<true, YFF, X3, A1_NW, A1_NS_F32>
         <<<blocks, A1_NW * 32, A1_NW * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
