@@ -9,13 +9,13 @@
 // and L2 atomics.
 //
 // aprod 1 streams 64-row records into shared memory with TMA bulk copies
-// (double-buffered per warp) so that DRAM latency is off the critical path;
-// the x gathers (L2-resident) are issued for both rows of a lane at once and
-// accumulated in six independent chains per row.
+// (double-buffered per pair of warps, one row per lane) so that DRAM latency
+// is off the critical path; the x gathers (L2-resident) of a row are issued at
+// once and accumulated in five independent chains.
 // aprod 2 is three kernels that run concurrently on two streams:
 //   astro+glob  per-star sums over star-sorted records (segmented warp scan),
-//   instr       per tile of up to 2048 rows, entries in rounds of distinct
-//               bins added into a float-pair shared-memory histogram,
+//   instr       per tile of up to 2048 rows, entries added into a float-pair
+//               shared-memory histogram by compare-and-swap,
 //   att         start-knot-ordered copy, sliding 4-knot window per axis.
 #include <algorithm>
 
@@ -126,19 +126,6 @@ __device__ __forceinline__ ff ldx(const float2* __restrict__ x, int64_t j) {
   return ff{a.x, a.y};
 }
 
-// Coefficient of slot t for row c (0/1) of the lane, from a record in smem or gmem.
-template <bool F32>
-__device__ __forceinline__ ff rec_val(const unsigned char* rec, int t, int lane, int c);
-template <>
-__device__ __forceinline__ ff rec_val<false>(const unsigned char* rec, int t, int lane, int c) {
-  const float4 v = *reinterpret_cast<const float4*>(rec + slot_offset<false>(t) + lane * 16);
-  return c == 0 ? ff{v.x, v.y} : ff{v.z, v.w};
-}
-template <>
-__device__ __forceinline__ ff rec_val<true>(const unsigned char* rec, int t, int lane, int c) {
-  const float2 v = *reinterpret_cast<const float2*>(rec + slot_offset<true>(t) + lane * 8);
-  return ff{c == 0 ? v.x : v.y, 0.0f};
-}
 template <bool F32>
 __device__ __forceinline__ ff val_mul(ff v, ff u) {
   if constexpr (F32) return f_mul(v.h, u);
@@ -150,229 +137,17 @@ __device__ __forceinline__ ff val_mul(ff v, ff u) {
 // y_knot[pos(r)] = y[r] (the knot-ordered copy aprod 2 reads) and a
 // deterministic ||y||^2 into *norm_out. coef is *coef_dev if given. y is a
 // float-pair vector (YFF, LSQR) or a double vector (the C ABI).
-// One CTA per SM, NW warps; each warp owns NS record buffers in shared memory
-// that lane 0 refills with TMA while the warp computes on the previous one.
+// One CTA per SM with NP pairs of warps. A pair owns NS record buffers in
+// shared memory that TMA refills while the pair computes on the others; the
+// two warps of a pair take one half of each record (lane l: row 32 h + l),
+// and the warp that finishes a buffer second refills it (a counter per buffer
+// in shared memory, acquire/release). The instrumental unknowns are gathered
+// from the block's shared memory when they fit beside the buffers
+// (instr_in_smem), otherwise through L1/L2.
 // ---------------------------------------------------------------------------
-constexpr int A1_PF = 1;  // records a warp keeps in flight towards L2 beyond its buffers
+constexpr int A1_PF = 1;  // records a pair keeps in flight towards L2 beyond its buffers
 
-template <bool F32, bool YFF, bool X3, int NW, int NS>
-__global__ void __launch_bounds__(NW * 32, 1)
-    k_aprod1(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
-             void* __restrict__ yv, const double* __restrict__ coef_dev, double coef_host,
-             float2* __restrict__ y_knot, double* part, unsigned int* counter, double* norm_out,
-             const double* stop, int instr_in_smem) {
-  if (stop && *stop != 0.0) return;
-  using R = Rec<F32>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[NW * NS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char* stage0 = smem + (size_t)wid * NS * R::BYTES;
-  // instrumental unknowns (small sets) are gathered from shared memory
-  float2* xi_s = reinterpret_cast<float2*>(smem + (size_t)NW * NS * R::BYTES);
-  if (instr_in_smem) {
-    for (int i = threadIdx.x; i < L.n_instr; i += blockDim.x) xi_s[i] = __ldg(x + L.instr_base + i);
-    __syncthreads();
-  }
-  const double4_32a* __restrict__ x3q = reinterpret_cast<const double4_32a*>(x3);
-  uint64_t* bar = bars + wid * NS;
-  const int64_t gw = (int64_t)blockIdx.x * NW + wid, nw = (int64_t)gridDim.x * NW;
-  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
-  const double coef = coef_dev ? *coef_dev : coef_host;
-  const ff coef_ff = ff_from_double(coef);
-  const bool glob = L.n_glob == 1;
-  const ff xg = glob ? ldx(x, L.glob_col) : ff_zero();
-
-  if (lane == 0) {
-#pragma unroll
-    for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
-    fence_proxy_async();
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int64_t r = gw + s * nw;
-      if (r < L.n_recs) {
-        mbar_expect_tx(&bar[s], R::BYTES);
-        tma_load(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < A1_PF; ++k) {
-      const int64_t rp = gw + (NS + k) * nw;
-      if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
-    }
-  }
-  __syncwarp();
-
-  ff nrm = ff_zero();
-  double nrm_d = 0.0;
-  uint32_t parity = 0;
-  bool ok = true;
-  int s = 0;
-  for (int64_t r = gw; r < L.n_recs; r += nw) {
-    const unsigned char* rec = stage0 + s * R::BYTES;
-    const int64_t row0 = r * REC_ROWS + 2 * lane;
-    ff yo[2] = {ff_zero(), ff_zero()};
-    double yd[2] = {0.0, 0.0};
-    if constexpr (YFF) {
-      const float2* y = static_cast<const float2*>(yv);
-      if (row0 + 1 < L.n_rows) {
-        const float4 a = *reinterpret_cast<const float4*>(y + row0);
-        yo[0] = ff{a.x, a.y};
-        yo[1] = ff{a.z, a.w};
-      } else if (row0 < L.n_rows) {
-        const float2 a = y[row0];
-        yo[0] = ff{a.x, a.y};
-      }
-    } else {
-      const double* y = static_cast<const double*>(yv);
-      if (row0 + 1 < L.n_rows) {
-        const double2 a = *reinterpret_cast<const double2*>(y + row0);
-        yd[0] = a.x;
-        yd[1] = a.y;
-      } else if (row0 < L.n_rows) {
-        yd[0] = y[row0];
-      }
-    }
-    // bounded, warp-uniform wait for this record
-    bool got = false;
-    for (int i = 0; i < WAIT_LIMIT; ++i)
-      if (__all_sync(0xffffffffu, mbar_try_wait(&bar[s], (parity >> s) & 1u))) {
-        got = true;
-        break;
-      }
-    if (!got) {
-      if (lane == 0) atomicExch(L.err, GSR_E_TIMEOUT);
-      ok = false;
-      break;
-    }
-    parity ^= 1u << s;
-
-    const int2 st = *reinterpret_cast<const int2*>(rec + R::STAR + lane * 8);
-    const int2 sk = *reinterpret_cast<const int2*>(rec + R::ATT_S + lane * 8);
-    const int st_c[2] = {st.x, st.y};
-    const int sk_c[2] = {sk.x, sk.y};
-    ushort2 ik[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      ik[k] = *reinterpret_cast<const ushort2*>(rec + R::INSTR_I + k * 128 + lane * 4);
-
-    // gather x for both rows: astrometric from L2 (lanes share stars), the 12
-    // attitude unknowns as three 32-byte loads from the knot-interleaved copy,
-    // instrumental from shared memory (or L1/L2)
-    ff xv[2][NSLOT];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-#pragma unroll
-      for (int t = 0; t < 5; ++t) xv[c][t] = ldx(x, 5 * (int64_t)st_c[c] + t);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if constexpr (X3) {
-          const double4_32a q = x3q[(int64_t)sk_c[c] * 3 + a];
-          xv[c][5 + 4 * a + 0] = ff_lo(q.x);
-          xv[c][5 + 4 * a + 1] = ff_lo(q.y);
-          xv[c][5 + 4 * a + 2] = ff_lo(q.z);
-          xv[c][5 + 4 * a + 3] = ff_lo(q.w);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            xv[c][5 + 4 * a + i] = ldx(x, L.att_base + a * L.n_knots + sk_c[c] + i);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int bin = c == 0 ? ik[k].x : ik[k].y;
-        if (instr_in_smem) {
-          const float2 v = xi_s[bin];
-          xv[c][17 + k] = ff{v.x, v.y};
-        } else {
-          xv[c][17 + k] = ldx(x, L.instr_base + bin);
-        }
-      }
-      xv[c][23] = xg;
-    }
-    // six independent accumulation chains per row: astro, 3 attitude axes,
-    // instrumental (+ global), combined by a tree at the end
-    ff part_acc[2][5];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-#pragma unroll
-      for (int g = 0; g < 5; ++g) part_acc[c][g] = ff_zero();
-#pragma unroll
-      for (int t = 0; t < NSLOT; ++t) {
-        if (t == 23 && !glob) continue;
-        const int g = t < 5 ? 0 : t < 9 ? 1 : t < 13 ? 2 : t < 17 ? 3 : 4;
-        part_acc[c][g] =
-            ff_add(part_acc[c][g], val_mul<F32>(rec_val<F32>(rec, t, lane, c), xv[c][t]));
-      }
-    }
-    ff acc[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-      acc[c] = ff_add(ff_add(ff_add(part_acc[c][0], part_acc[c][1]),
-                             ff_add(part_acc[c][2], part_acc[c][3])),
-                      part_acc[c][4]);
-    const int2 ps = *reinterpret_cast<const int2*>(rec + R::POS + lane * 8);
-    if constexpr (YFF) {
-      float2* y = static_cast<float2*>(yv);
-      ff yn[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) yn[c] = ff_norm(ff_add(ff_mul(coef_ff, yo[c]), acc[c]));
-      if (row0 + 1 < L.n_rows) {
-        *reinterpret_cast<float4*>(y + row0) = make_float4(yn[0].h, yn[0].l, yn[1].h, yn[1].l);
-        nrm = ff_add(nrm, ff_add(ff_mul(yn[0], yn[0]), ff_mul(yn[1], yn[1])));
-        if (y_knot) {
-          y_knot[ps.x] = make_float2(yn[0].h, yn[0].l);
-          y_knot[ps.y] = make_float2(yn[1].h, yn[1].l);
-        }
-      } else if (row0 < L.n_rows) {
-        y[row0] = make_float2(yn[0].h, yn[0].l);
-        nrm = ff_add(nrm, ff_mul(yn[0], yn[0]));
-        if (y_knot) y_knot[ps.x] = make_float2(yn[0].h, yn[0].l);
-      }
-    } else {
-      double* y = static_cast<double*>(yv);
-      const double yn0 = __fma_rn(coef, yd[0], ff_to_double(acc[0]));
-      const double yn1 = __fma_rn(coef, yd[1], ff_to_double(acc[1]));
-      if (row0 + 1 < L.n_rows) {
-        *reinterpret_cast<double2*>(y + row0) = make_double2(yn0, yn1);
-        nrm_d = __fma_rn(yn0, yn0, __fma_rn(yn1, yn1, nrm_d));
-      } else if (row0 < L.n_rows) {
-        y[row0] = yn0;
-        nrm_d = __fma_rn(yn0, yn0, nrm_d);
-      }
-    }
-    // every lane is done with this buffer: refill it with the record NS steps ahead
-    __syncwarp();
-    if (lane == 0) {
-      const int64_t rn = r + NS * nw;
-      if (rn < L.n_recs) {
-        fence_proxy_async();
-        mbar_expect_tx(&bar[s], R::BYTES);
-        tma_load(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s]);
-      }
-      // A1_PF records further ahead go to L2 only, so that the copies find
-      // their records there when their turn comes
-      const int64_t rp = rn + A1_PF * nw;
-      if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
-    }
-    s = (s + 1 == NS) ? 0 : s + 1;
-  }
-  if (!ok) {
-    // give copies still in flight on this warp's buffers a bounded chance to land
-    for (int q = 0; q < NS; ++q)
-      for (int i = 0; i < WAIT_LIMIT / 16; ++i)
-        if (mbar_try_wait(&bar[q], (parity >> q) & 1u)) break;
-  }
-  if (norm_out) grid_sum_store(YFF ? ff_to_double(nrm) : nrm_d, part, counter, norm_out);
-}
-
-// ---------------------------------------------------------------------------
-// aprod 1, warp-pair form: the same computation as k_aprod1 with NP pairs of
-// warps per block. The two warps of a pair share the pair's NS record buffers
-// and take one half of each record (lane l: row 32 h + l of the record); the
-// warp that finishes a buffer second refills it (a counter per buffer in
-// shared memory, acquire/release), so twice as many warps share the same
-// shared memory as in k_aprod1.
-// ---------------------------------------------------------------------------
+// Coefficient of slot t for row ri of a record in shared memory.
 template <bool F32>
 __device__ __forceinline__ ff rec_val1(const unsigned char* rec, int t, int ri) {
   if constexpr (F32) {
@@ -394,7 +169,7 @@ __device__ __forceinline__ uint32_t smem_add_acq_rel(uint32_t* c) {
 
 template <bool F32, bool YFF, bool X3, int NP, int NS>
 __global__ void __launch_bounds__(NP * 64, 1)
-    k_aprod1p(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
+    k_aprod1(Layout L, const float2* __restrict__ x, const float2* __restrict__ x3,
               void* __restrict__ yv, const double* __restrict__ coef_dev, double coef_host,
               float2* __restrict__ y_knot, double* part, unsigned int* counter, double* norm_out,
               const double* stop, int instr_in_smem) {
@@ -972,11 +747,9 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-constexpr int A1_NW = 6;                    // warps per aprod 1 block (one block per SM)
-constexpr int A1_NS_FF = 2, A1_NS_F32 = 3;  // record buffers per warp
+constexpr int A1_NP = 6;                    // warp pairs per aprod 1 block (one block per SM)
+constexpr int A1_NS_FF = 2, A1_NS_F32 = 3;  // record buffers per warp pair
 constexpr int A1_XI_SMEM_MAX = 6144;        // instrumental unknowns staged in shared memory
-// warp pairs (k_aprod1p) instead of one warp per record buffer set (k_aprod1)
-constexpr bool A1_PAIRS = true;
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSR_OK : GSR_E_CUDA; }
 
@@ -985,31 +758,19 @@ int set_kernel_attributes() {
   auto C = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  const int ff_bytes = A1_NW * A1_NS_FF * Rec<false>::BYTES + A1_XI_SMEM_MAX * 8;
-  const int f32_bytes = A1_NW * A1_NS_F32 * Rec<true>::BYTES + A1_XI_SMEM_MAX * 8;
-  C(cudaFuncSetAttribute(k_aprod1<false, true, true, A1_NW, A1_NS_FF>,
+  const int ff_bytes = A1_NP * A1_NS_FF * Rec<false>::BYTES + A1_XI_SMEM_MAX * 8;
+  const int f32_bytes = A1_NP * A1_NS_F32 * Rec<true>::BYTES + A1_XI_SMEM_MAX * 8;
+  C(cudaFuncSetAttribute(k_aprod1<false, true, true, A1_NP, A1_NS_FF>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1<false, false, true, A1_NW, A1_NS_FF>,
+  C(cudaFuncSetAttribute(k_aprod1<false, false, true, A1_NP, A1_NS_FF>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1<false, false, false, A1_NW, A1_NS_FF>,
+  C(cudaFuncSetAttribute(k_aprod1<false, false, false, A1_NP, A1_NS_FF>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1<true, true, true, A1_NW, A1_NS_F32>,
+  C(cudaFuncSetAttribute(k_aprod1<true, true, true, A1_NP, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod1<true, false, true, A1_NW, A1_NS_F32>,
+  C(cudaFuncSetAttribute(k_aprod1<true, false, true, A1_NP, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod1<true, false, false, A1_NW, A1_NS_F32>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<false, true, true, A1_NW, A1_NS_FF>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<false, false, true, A1_NW, A1_NS_FF>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<false, false, false, A1_NW, A1_NS_FF>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, ff_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<true, true, true, A1_NW, A1_NS_F32>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<true, false, true, A1_NW, A1_NS_F32>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
-  C(cudaFuncSetAttribute(k_aprod1p<true, false, false, A1_NW, A1_NS_F32>,
+  C(cudaFuncSetAttribute(k_aprod1<true, false, false, A1_NP, A1_NS_F32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, f32_bytes));
 #define GSR_INSTR_ATTR(F, B, T)                                                             \
   C(cudaFuncSetAttribute(k_aprod2_instr<F, B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -1071,32 +832,19 @@ static int launch_aprod1_t(gsr_system* sys, int which_values, const float2* x_ff
     return GSR_OK;
   }
   int blocks = sys->num_sms;
-  const int64_t need = (L.n_recs + A1_NW - 1) / A1_NW;
+  const int64_t need = (L.n_recs + A1_NP - 1) / A1_NP;
   if (need < blocks) blocks = (int)need;
   const int xi = L.n_instr <= A1_XI_SMEM_MAX ? 1 : 0;
   const int xib = xi ? (int)L.n_instr * 8 : 0;
-  if (A1_PAIRS) {
-    // A1_NW pairs of warps share A1_NW buffer sets: twice the warps of k_aprod1
-    if (which_values == GSR_VALUES_F32)
-      k_aprod1p<true, YFF, X3, A1_NW, A1_NS_F32>
-          <<<blocks, A1_NW * 64, A1_NW * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
-              L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
-              norm_slot, stop, xi);
-    else
-      k_aprod1p<false, YFF, X3, A1_NW, A1_NS_FF>
-          <<<blocks, A1_NW * 64, A1_NW * A1_NS_FF * Rec<false>::BYTES + xib, st>>>(
-              L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
-              norm_slot, stop, xi);
-    return cuda_status(cudaGetLastError());
-  }
+  // A1_NP pairs of warps, each pair with its own record buffers
   if (which_values == GSR_VALUES_F32)
-    k_aprod1<true, YFF, X3, A1_NW, A1_NS_F32>
-        <<<blocks, A1_NW * 32, A1_NW * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
+    k_aprod1<true, YFF, X3, A1_NP, A1_NS_F32>
+        <<<blocks, A1_NP * 64, A1_NP * A1_NS_F32 * Rec<true>::BYTES + xib, st>>>(
             L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
             norm_slot, stop, xi);
   else
-    k_aprod1<false, YFF, X3, A1_NW, A1_NS_FF>
-        <<<blocks, A1_NW * 32, A1_NW * A1_NS_FF * Rec<false>::BYTES + xib, st>>>(
+    k_aprod1<false, YFF, X3, A1_NP, A1_NS_FF>
+        <<<blocks, A1_NP * 64, A1_NP * A1_NS_FF * Rec<false>::BYTES + xib, st>>>(
             L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
             norm_slot, stop, xi);
   return cuda_status(cudaGetLastError());
