@@ -1,8 +1,8 @@
 /*
  * gsr.h - C ABI of libgsr, a single-GPU (B300, sm_103a) implementation of the
  * hot path of the Gaia AVU-GSR solver (arXiv 2503.22863):
- *   aprod 1  y += A x      (Sec. 2.1, Eq. 2)
- *   aprod 2  x += A^T y    (Sec. 2.1, Eq. 3)
+ *   aprod 1  y += A x      (Sec. 2, Eq. 2)
+ *   aprod 2  x += A^T y    (Sec. 2, Eq. 3)
  *   preconditioned LSQR on A x = b (Sec. 2, Eq. 1; solver steps 2-5 of Sec. 2),
  *   the Paige-Saunders algorithm cited in Sec. 1.
  *
