@@ -71,10 +71,19 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel, n_rows):
-    """DRAM bytes per launch (read + write) from the committed ncu summary of the
-    kernel group on the small workload, scaled to n_rows (the traffic of these
-    row-streaming kernels grows with the rows processed), if that summary was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per launch (read + write) of the kernel group, from a committed
+    ncu summary taken on the current kernel source (else None): the one-pass
+    capture of this very workload when there is one (profiles/dram_medium.md),
+    otherwise the small-workload capture scaled to n_rows (the traffic of these
+    row-streaming kernels grows about in proportion to the rows processed)."""
+    p = os.path.join(ROOT, "profiles", "dram_medium.md")
+    if os.path.exists(p):
+        text = open(p).read()
+        m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+        nr = re.search(r"n_rows:\s*(\d+)", text)
+        t = re.search(r"%s_bytes_per_launch:\s*([0-9.eE+]+)" % kernel, text)
+        if m and nr and t and m.group(1) == kernel_source_hash() and int(nr.group(1)) == n_rows:
+            return float(t.group(1))
     p = os.path.join(ROOT, "profiles", "%s_small.md" % kernel)
     if not os.path.exists(p):
         return None
