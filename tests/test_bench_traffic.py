@@ -1,0 +1,61 @@
+"""Host logic of the benchmark's roofline `traffic` field: DRAM bytes per launch
+come from a committed ncu summary only while that summary was taken on the
+current kernel source; a one-pass capture of the very workload wins over the
+small-workload counters scaled by rows."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _use(tmp_path, monkeypatch, h):
+    """Profiles under tmp_path; the source hash is the repository's (h)."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+
+
+def _write_profiles(tmp_path, h, medium=True):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "aprod1_small.md").write_text(
+        "kernel_source_hash: %s\n\ndram_bytes_per_row: 240.5\n" % h)
+    (prof / "aprod2_small.md").write_text(
+        "kernel_source_hash: %s\n\ndram_bytes_per_row: 250.0\n" % h)
+    if medium:
+        (prof / "dram_medium.md").write_text(
+            "kernel_source_hash: %s\nn_rows: 1000\n\naprod1_bytes_per_launch: 262000\n"
+            "aprod2_bytes_per_launch: 251000\n" % h)
+
+
+def test_direct_capture_wins_for_its_workload(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    _write_profiles(tmp_path, h)
+    _use(tmp_path, monkeypatch, h)
+    assert bench.profiled_traffic("aprod1", 1000) == 262000.0
+    assert bench.profiled_traffic("aprod2", 1000) == 251000.0
+
+
+def test_other_workloads_scale_the_small_counters(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    _write_profiles(tmp_path, h)
+    _use(tmp_path, monkeypatch, h)
+    assert bench.profiled_traffic("aprod1", 2000) == 240.5 * 2000
+    assert bench.profiled_traffic("aprod2", 3) == 250.0 * 3
+
+
+def test_no_direct_capture(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    _write_profiles(tmp_path, h, medium=False)
+    _use(tmp_path, monkeypatch, h)
+    assert bench.profiled_traffic("aprod1", 1000) == 240.5 * 1000
+
+
+def test_stale_summaries_give_none(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    assert h != "0123456789abcdef"
+    _write_profiles(tmp_path, "0123456789abcdef")
+    _use(tmp_path, monkeypatch, h)
+    assert bench.profiled_traffic("aprod1", 1000) is None
+    assert bench.profiled_traffic("aprod2", 5) is None
