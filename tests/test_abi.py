@@ -131,3 +131,15 @@ def test_batch_entry_points_validate_arguments(gsr):
         assert lib.gsr_aprod2_batch(None, k, p, p, None) == E_ARG
     t = ctypes.c_int()
     assert lib.gsr_batch_tuning(None, ctypes.byref(t), ctypes.byref(t)) == E_ARG
+
+
+def test_binding_refuses_host_tensors(gsr):
+    # the binding marshals device pointers only: a host tensor is an error, not
+    # a silent copy or a CPU path
+    import torch
+    with pytest.raises(TypeError):
+        gsr._dptr(torch.zeros(3, dtype=torch.float64), 3, "x")
+    with pytest.raises(TypeError):
+        gsr._dptr2(torch.zeros((3, 2), dtype=torch.float64), 3, 2, "X")
+    with pytest.raises(TypeError):
+        gsr._dptr(np.zeros(3), 3, "x")
