@@ -51,7 +51,7 @@ typedef enum {
   GSR_E_NONFINITE = 4,   /* NaN or Inf in the matrix or right-hand side */
   GSR_E_OOM = 5,         /* device allocation failed */
   GSR_E_CUDA = 6,        /* a CUDA runtime call failed */
-  GSR_E_TIMEOUT = 7,     /* a bounded device-side wait ran out */
+  GSR_E_TIMEOUT = 7,     /* a bounded device-side wait or retry loop ran out */
   GSR_E_UNSUPPORTED = 8  /* sizes beyond this build's limits (see gsr_create) */
 } gsr_status;
 
