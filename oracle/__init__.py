@@ -18,6 +18,7 @@ Pins (each checked by a CPU test, see ``tests/test_oracle_*.py``):
 from .core import (  # noqa: F401
     build_oracle,
     n_unknowns,
+    n_equations,
     aprod1,
     aprod2,
     colnorm2,

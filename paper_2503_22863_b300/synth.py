@@ -157,3 +157,50 @@ def mlp_init_params(seed):
     return np.concatenate([g.normal(0.0, math.sqrt(2.0 / 8), 64 * 8), np.zeros(64),
                            g.normal(0.0, math.sqrt(2.0 / 64), 64 * 64), np.zeros(64),
                            g.normal(0.0, math.sqrt(1.0 / 64), 64), np.zeros(1)])
+
+
+def rank_deficient_system(seed=35):
+    """An overdetermined, rank-deficient system (for the minimum-norm checks).
+
+    120 stars of 1, 2, 3, 4 or 40 observations (a star with fewer than 5 rows
+    leaves its 5 astrometric columns rank-deficient), attitude start knots
+    restricted to [0, 45] of 100 (knots 49..99 have no rows: empty columns),
+    and the coefficients of instrumental columns 0..4 set to zero (empty
+    columns as well). About 2,200 rows, 951 unknowns.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed + 1)))
+    counts = rng.choice([1, 2, 3, 4, 40], size=120, p=[0.15, 0.15, 0.15, 0.15, 0.4])
+    s = make_system(n_stars=120, n_knots=100, n_instr=50, n_glob=1, counts=counts, seed=seed)
+    att = 5 * 120 + (s["att_off"] - 5 * 120) % 46
+    vals = s["vals"].copy()
+    vals[:, 17:23][s["instr"] < 5] = 0.0
+    return dict(s, vals=vals, att_off=att)
+
+
+def add_constraints(sys, n_con=6, per_row=200, seed=0, must_cols=None):
+    """The system with n_con constraint rows appended (CSR arrays con_ptr,
+    con_col, con_val): each row has per_row distinct columns, four fifths
+    astrometric columns of random stars and the rest attitude, instrumental
+    or global columns, coefficients N(0, 1). must_cols (optional) are columns
+    every row also includes (e.g. those of rank-deficient stars). The
+    right-hand side's constraint part is formed by whichever side uses it."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    n_unk = n_unknowns(sys["n_stars"], sys["n_knots"], sys["n_instr"], sys["n_glob"])
+    n_astro = 5 * sys["n_stars"]
+    ptr, cols, vals = [0], [], []
+    for _ in range(n_con):
+        na = min(n_astro, (4 * per_row) // 5)
+        c = set(rng.choice(n_astro, size=na, replace=False).tolist())
+        if n_unk > n_astro:
+            c |= set((n_astro + rng.choice(n_unk - n_astro, size=min(n_unk - n_astro,
+                                                                      per_row - na),
+                                           replace=False)).tolist())
+        if must_cols is not None:
+            c |= set(int(j) for j in must_cols)
+        c = np.array(sorted(c), dtype=np.int64)
+        cols.append(c)
+        vals.append(rng.standard_normal(c.size))
+        ptr.append(ptr[-1] + c.size)
+    return dict(sys, con_ptr=np.array(ptr, dtype=np.int64),
+                con_col=np.concatenate(cols) if cols else np.zeros(0, np.int64),
+                con_val=np.concatenate(vals) if vals else np.zeros(0))

@@ -32,12 +32,25 @@ def n_unk(sys):
     return 5 * sys["n_stars"] + 3 * sys["n_knots"] + sys["n_instr"] + sys["n_glob"]
 
 
+def n_con(sys):
+    return 0 if sys.get("con_ptr") is None else len(sys["con_ptr"]) - 1
+
+
 def sparse(sys):
+    """A as a sparse matrix: the observation rows, then any constraint rows
+    (CSR con_ptr / con_col / con_val, repeated columns summed)."""
     cols = columns(sys)
     rows = np.repeat(np.arange(sys["n_rows"]), 24).reshape(-1, 24)
     keep = cols >= 0
-    return sp.csr_matrix((np.asarray(sys["vals"])[keep], (rows[keep], cols[keep])),
-                         shape=(sys["n_rows"], n_unk(sys)))
+    r, c, v = rows[keep], cols[keep], np.asarray(sys["vals"])[keep]
+    nc = n_con(sys)
+    if nc:
+        ptr = np.asarray(sys["con_ptr"])
+        crow = sys["n_rows"] + np.repeat(np.arange(nc), np.diff(ptr))
+        r = np.concatenate([r, crow])
+        c = np.concatenate([c, np.asarray(sys["con_col"])])
+        v = np.concatenate([v, np.asarray(sys["con_val"])])
+    return sp.csr_matrix((v, (r, c)), shape=(sys["n_rows"] + nc, n_unk(sys)))
 
 
 def dense(sys):

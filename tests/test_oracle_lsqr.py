@@ -6,7 +6,7 @@ import scipy.sparse.linalg as spla
 
 import oracle
 from paper_2503_22863_b300 import synth
-from dense_ref import dense, sparse
+from dense_ref import columns, dense, sparse
 
 
 def rhs(sys, consistent=False):
@@ -89,6 +89,28 @@ def test_stopping_rule_matches_scipy():
     assert abs(res["rnorm"] - out[3]) <= 1e-10 * out[3]
 
 
+def test_stopping_rule_on_the_preconditioned_system():
+    # The loop runs on A D (Sec. 2, solver step 2) and de-preconditions after it
+    # (step 5): its stopping tests use ||A D|| and the norm of the iterate z of
+    # A D z = b, as scipy's LSQR does when given A D. Columns spread over 1e-8 ..
+    # 1e8 make ||x|| = ||D z|| and ||z|| differ by orders of magnitude, so a test
+    # on ||x|| would stop at a different iteration (here: at the first).
+    sys = synth.make_system(**SMALL)
+    C = 10.0 ** np.random.default_rng(8).uniform(-8, 8, oracle.n_unknowns(sys))
+    cols = columns(sys)
+    sys = dict(sys, vals=sys["vals"] * np.where(cols >= 0, C[np.maximum(cols, 0)], 0.0))
+    b = rhs(sys)
+    A = sparse(sys)
+    c = np.sqrt(np.asarray(A.multiply(A).sum(axis=0))).ravel()
+    Ad = A @ sps.diags(1.0 / c)
+    for tol in (1e-6, 1e-10):
+        res = oracle.lsqr(sys, b, atol=tol, btol=tol, conlim=1e8)
+        out = spla.lsqr(Ad, b, atol=tol, btol=tol, conlim=1e8, iter_lim=10000)
+        assert res["istop"] == out[1], tol
+        assert abs(res["itn"] - out[2]) <= 1, (tol, res["itn"], out[2])
+        assert res["itn"] > 10
+
+
 def test_residual_estimates_and_monotonicity():
     sys = synth.make_system(**SMALL)
     b = rhs(sys)
@@ -160,3 +182,55 @@ def test_tiny_config_solution_vs_dense():
     x_ne = np.linalg.solve(AtA, A.T @ b)
     err = np.linalg.norm(res["x"] - x_ne) / np.linalg.norm(x_ne)
     assert err < 1e-10, err
+
+
+def test_rank_deficient_minimum_norm():
+    # Rank-deficient A (stars with 1-4 rows, empty knot and instrumental
+    # columns): LSQR from x0 = 0 on A D converges to the minimum-norm solution
+    # of the scaled problem, x = D pinv(A D) b, with x_j = 0 on empty columns.
+    sys = synth.rank_deficient_system()
+    b = rhs(sys)
+    A = dense(sys)
+    c = np.sqrt((A ** 2).sum(axis=0))
+    assert (c == 0).sum() > 100 and np.linalg.matrix_rank(A) < A.shape[1] - (c == 0).sum()
+    d = np.where(c > 0, 1.0 / np.where(c > 0, c, 1.0), 1.0)
+    x_pin = d * (np.linalg.pinv(A * d[None, :], rcond=1e-12) @ b)
+    res = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
+    assert res["istop"] in (1, 2)
+    assert np.linalg.norm(res["x"] - x_pin) / np.linalg.norm(x_pin) < 1e-12
+    assert not res["x"][c == 0].any()
+
+
+@pytest.mark.parametrize("params", [
+    dict(n_stars=1, n_knots=4, n_instr=6, n_glob=1, obs=60, poisson=False, seed=42),
+    dict(n_stars=2, n_knots=5, n_instr=6, n_glob=0, obs=100, poisson=False, seed=43),
+])
+def test_covariance_pairs_vs_dense_inverse(params):
+    # Sec. 2.2, Eq. 4 read with the variance's direction vectors: after exactly
+    # n = N_unk steps, sum_k d_k d_k^T = (A^T A)^{-1} in exact arithmetic, so
+    # each pair's estimate is the (j1, j2) entry of the dense inverse. As for
+    # the variance, only tiny systems whose run takes all n steps pin it (LSQR
+    # that stops early at machine precision has explored less than the whole
+    # space); the tolerance is the variance's, relative to sqrt(var_j1 var_j2)
+    # because a covariance can be near zero. The run is column-scaled (as the
+    # solver's is), so a missing de-preconditioning factor d_j1 d_j2 would be an
+    # O(1) error. Every pair j1 <= j2 is checked; a
+    # pair (j, j) must equal the variance exactly (the same sum), and swapping
+    # the two indexes must change nothing.
+    sys = synth.make_system(**params)
+    b = rhs(sys)
+    A = dense(sys)
+    n = A.shape[1]
+    inv = np.linalg.inv(A.T @ A)
+    j1, j2 = np.triu_indices(n)
+    pairs = np.stack([j1, j2], axis=1)
+    res = oracle.lsqr(sys, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=n, want_var=True,
+                      cov_pairs=pairs)
+    assert res["itn"] == n
+    ref = inv[j1, j2]
+    den = np.sqrt(np.diag(inv)[j1] * np.diag(inv)[j2])
+    assert np.max(np.abs(res["cov"] - ref) / den) < 1e-3
+    diag = j1 == j2
+    np.testing.assert_array_equal(res["cov"][diag], res["var"][j1[diag]])
+    sw = oracle.lsqr(sys, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=n, cov_pairs=pairs[:, ::-1])
+    np.testing.assert_array_equal(sw["cov"], res["cov"])
