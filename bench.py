@@ -18,7 +18,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -71,28 +70,25 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel, n_rows):
-    """DRAM bytes per launch (read + write) of the kernel group, from a committed
-    ncu summary taken on the current kernel source (else None): the one-pass
-    capture of this very workload when there is one (profiles/dram_medium.md),
-    otherwise the small-workload capture scaled to n_rows (the traffic of these
+    """DRAM bytes per launch (read + write) of the kernel group from the ncu
+    figures in profiles/traffic.json, taken on the current kernel source (else
+    None): a capture of this very workload when there is one, otherwise a
+    smaller workload's bytes per row scaled to n_rows (the traffic of these
     row-streaming kernels grows about in proportion to the rows processed)."""
-    p = os.path.join(ROOT, "profiles", "dram_medium.md")
-    if os.path.exists(p):
-        text = open(p).read()
-        m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-        nr = re.search(r"n_rows:\s*(\d+)", text)
-        t = re.search(r"%s_bytes_per_launch:\s*([0-9.eE+]+)" % kernel, text)
-        if m and nr and t and m.group(1) == kernel_source_hash() and int(nr.group(1)) == n_rows:
-            return float(t.group(1))
-    p = os.path.join(ROOT, "profiles", "%s_small.md" % kernel)
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    text = open(p).read()
-    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_row:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
-        return None
-    return float(t.group(1)) * n_rows
+    with open(p) as f:
+        entries = json.load(f).get("entries", [])
+    h = kernel_source_hash()
+    cur = [e for e in entries if e.get("kernel") == kernel and e.get("kernel_source_hash") == h]
+    for e in cur:
+        if e.get("n_rows") == n_rows and "bytes_per_launch" in e:
+            return float(e["bytes_per_launch"])
+    for e in cur:
+        if "bytes_per_row" in e:
+            return float(e["bytes_per_row"]) * n_rows
+    return None
 
 
 class ClockSampler:
@@ -160,6 +156,33 @@ def cpu_oracle_estimate(sys, b, iters):
     t2 = time.perf_counter() - t0
     per_iter = max(t2 - t1, 1e-9)
     return t1 + (iters - 1) * per_iter, per_iter, t1
+
+
+def cpu_aprod_times(sys_, n_threads_note=None):
+    """Seconds per aprod 1 and aprod 2 of the single-core oracle and of the
+    all-core OpenMP baseline on `sys_` (median of a few runs; inputs seeded)."""
+    import cpu_baseline
+    import oracle
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(sys_["n_unk"])
+    y = rng.standard_normal(sys_["n_rows"])
+    out = {}
+    for name, a1, a2, reps in (("oracle", oracle.aprod1, oracle.aprod2, 1),
+                               ("openmp", cpu_baseline.aprod1, cpu_baseline.aprod2, 3)):
+        t1, t2 = [], []
+        for _ in range(reps):
+            yy = np.zeros(sys_["n_rows"])
+            t0 = time.perf_counter()
+            a1(sys_, x, yy)
+            t1.append(time.perf_counter() - t0)
+            xx = np.zeros(sys_["n_unk"])
+            t0 = time.perf_counter()
+            a2(sys_, y, xx)
+            t2.append(time.perf_counter() - t0)
+        out[name] = {"aprod1_s": statistics.median(t1), "aprod2_s": statistics.median(t2)}
+    out["openmp"]["threads"] = cpu_baseline.threads()
+    out["oracle"]["threads"] = 1
+    return out
 
 
 def make_workload(name):
@@ -466,6 +489,18 @@ def run_ours(args):
             e2e.append(time.perf_counter() - t0)
         barrier()
 
+        # iterations per second over the paper's 100-iteration run (Sec. 3): one
+        # solve that cannot stop before itnlim = 100
+        ev100 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        x100 = torch.empty_like(x)
+        ev100[0].record(stream)
+        r100 = S.lsqr(b, x=x100, atol=0.0, btol=0.0, conlim=0.0, itnlim=100)
+        ev100[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t100 = ev100[0].elapsed_time(ev100[1]) / 1e3
+        its_100 = r100["itn"] / t100
+        log("100-iteration solve: %.1f ms (%.0f iterations/s)" % (t100 * 1e3, its_100))
+
         variants = {}
         if args.variants:
             variants["mixed"] = bench_mixed(S, b, x_ref, args, stream, dev)
@@ -504,7 +539,10 @@ def run_ours(args):
                      "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
                      "traffic": profiled_traffic(dom, n_rows)},
         "aprod": {"aprod1_ms": t_a1, "aprod1_GBps": gbs1, "aprod2_ms": t_a2, "aprod2_GBps": gbs2,
-                  "vector_ms": t_vec, "iterations_per_s": 1e3 / (t_a1 + t_a2 + t_vec),
+                  "vector_ms": t_vec, "iterations_per_s": its_100,
+                  "iterations_per_s_how": "one solve of exactly 100 iterations (the paper's "
+                                          "run length, Sec. 3), CUDA events around it",
+                  "iterations_per_s_kernels_only": 1e3 / (t_a1 + t_a2 + t_vec),
                   "bytes_per_launch": {"aprod1": by1, "aprod2": by2}},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n_rows,
                 "d2h_bytes_per_step": 8 * n_unk},
@@ -523,6 +561,22 @@ def run_ours(args):
             "sample": "oracle LSQR with 1 and 2 iterations on the same system (%.1f s and %.1f s); "
                       "per-iteration %.2f s extrapolated to %d iterations" % (
                           t1, t1 + per_iter, per_iter, n_star)}
+        log("timing the oracle and the all-core OpenMP products ...")
+        cpu = cpu_aprod_times(sys_)
+        tiny = make_workload("tiny")
+        cpu_tiny = cpu_aprod_times(tiny)
+        omp = cpu["openmp"]
+        line["cpu_openmp"] = {
+            "kind": "all-core OpenMP aprod (independent of the oracle and the CUDA library)",
+            "cores": omp["threads"], "aprod1_s": omp["aprod1_s"], "aprod2_s": omp["aprod2_s"],
+            "lsqr_time_to_1e9_s_lower_bound": n_star * (omp["aprod1_s"] + omp["aprod2_s"]),
+            "lower_bound_how": "%d iterations x (aprod 1 + aprod 2), vector updates not counted"
+                               % n_star,
+            "gpu_speedup_per_aprod": {"aprod1": omp["aprod1_s"] / (t_a1 * 1e-3),
+                                      "aprod2": omp["aprod2_s"] / (t_a2 * 1e-3)}}
+        line["cpu_baseline"]["oracle_aprod_s"] = {
+            args.workload: cpu["oracle"], "tiny": cpu_tiny["oracle"]}
+        line["cpu_openmp"]["tiny"] = cpu_tiny["openmp"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     S.close()

@@ -26,11 +26,26 @@
  *   - "stream" is a cudaStream_t (NULL = the legacy default stream). Calls are
  *     stream-ordered and asynchronous unless stated otherwise.
  *   - Every call returns a gsr_status; nothing aborts or prints.
- *     gsr_strerror() gives the text. After GSR_E_CUDA the system should be
- *     destroyed.
+ *     gsr_strerror() gives the text. After GSR_E_CUDA or GSR_E_TIMEOUT the
+ *     system should be destroyed: a device wait that ran out may have left
+ *     copies into a block's shared memory unfinished and the results of that
+ *     launch incomplete.
  *   - Arithmetic: products and sums run as pairs of FP32 numbers with
  *     error-free transformations (about 48 significant bits, within 1e-13 of
  *     FP64 relative to |A||x|); vectors, norms and LSQR scalars are FP64.
+ *   - Range: any finite FP64 input is accepted, except the matrices
+ *     gsr_create rejects below. A float pair has FP32's exponent range, so the
+ *     library works on an exactly rescaled problem. gsr_create multiplies row
+ *     i by 2^e_i and column j by 2^g_j (powers of two, exact). It leaves a
+ *     matrix whose nonzero |A_ij| all lie in [2^-40, 2^40) as it is. Otherwise
+ *     it uses column exponents alone where that suffices, else row and column
+ *     exponents. Every call undoes the scaling exactly. A product call checks
+ *     its rescaled input vector: with every nonzero entry in [2^-60, 2^60) the
+ *     float-pair kernels run; otherwise the same call runs FP64 kernels (one
+ *     thread per row, several times slower, accurate to FP64 rounding). The
+ *     choice is made on the device, per call. LSQR scales b by a power of two
+ *     (its largest entry into [1, 2)) and scales x and the residual norms
+ *     back.
  */
 #ifndef GSR_H
 #define GSR_H
@@ -81,7 +96,16 @@ typedef struct {
  * instr outside [0, n_instr) or repeated in a row), GSR_E_UNSORTED (astro_off
  * decreasing), GSR_E_NONFINITE (NaN/Inf value), GSR_E_UNSUPPORTED (n_rows or
  * N_unk >= 2^31, or n_instr > 24576: the instrumental histogram of aprod 2
- * lives in one block's shared memory), GSR_E_OOM.
+ * lives in one block's shared memory; or coefficients too spread for the
+ * rescaling: after the library fits power-of-two row and column exponents to
+ * the binary exponents of A in the least-squares sense, a coefficient remains
+ * more than 2^100 below the largest of its column - every 2 x 2 minor with
+ * |a00 a11 / (a01 a10)| beyond about 2^204, such as [[1, 1e-70], [1, 1]], is
+ * one, since no diagonal scaling changes that ratio), GSR_E_OOM. All of these
+ * are decided on the host before the device is touched.
+ * Matrices whose rescaled coefficients still reach below 2^-40 of their row
+ * and column maxima are accepted; their products always run the FP64
+ * kernels.
  * On success *out owns everything; release it with gsr_destroy().
  */
 int gsr_create(const gsr_dims* dims, const double* vals, const int64_t* astro_off,
@@ -91,11 +115,41 @@ int gsr_create(const gsr_dims* dims, const double* vals, const int64_t* astro_of
 void gsr_destroy(gsr_system* sys);
 const char* gsr_strerror(int status);
 int64_t gsr_n_unknowns(const gsr_system* sys);
+/* Observation rows (the rows given to gsr_create). */
 int64_t gsr_n_rows(const gsr_system* sys);
 
-/* Eq. 2 (aprod 1): y[n_rows] += A x[N_unk]. x, y device; x is not modified. */
+/*
+ * Constraint equations (Sec. 2: the overdetermined system needs a set of
+ * constraint equations for a unique solution; Sec. 2.1: they are about 1% of
+ * the system and replicated on every process). The paper does not give their
+ * form, so they are generic sparse rows, appended to A after the n_rows
+ * observation rows. Host arrays in CSR form, copied during the call:
+ *   con_ptr int64  [n_con + 1]  row c holds entries con_ptr[c] .. con_ptr[c+1]-1,
+ *                               con_ptr[0] = 0, non-decreasing
+ *   con_col int64  [nnz]        column in [0, N_unk) (repeats allowed)
+ *   con_val double [nnz]        finite coefficient (any FP64 magnitude)
+ * Afterwards every vector over the equations - y of aprod 1 and aprod 2 and
+ * of their _values and _noalloc forms, b of gsr_lsqr_solve - has
+ * gsr_n_equations() = n_rows + n_con entries, the constraint rows last, and
+ * the column norms (and so the column preconditioner) include them. The
+ * constraint rows are computed in FP64 (a warp per segment of at most 1024
+ * entries). A call replaces earlier constraints; n_con = 0 removes them.
+ * The batched forms do not take constraint rows (GSR_E_UNSUPPORTED).
+ * Errors: GSR_E_ARG (sizes, pointers, con_ptr not non-decreasing from 0),
+ * GSR_E_INDEX (a column outside [0, N_unk)), GSR_E_NONFINITE, all on the host
+ * before the device is touched; GSR_E_OOM. Synchronises the stream.
+ */
+int gsr_set_constraints(gsr_system* sys, int64_t n_con, const int64_t* con_ptr,
+                        const int64_t* con_col, const double* con_val, void* stream);
+/* Equations of the system: n_rows + n_con. */
+int64_t gsr_n_equations(const gsr_system* sys);
+
+/* Eq. 2 (aprod 1): y[n_eq] += A x[N_unk] (n_eq = gsr_n_equations: the
+ * observation rows, then any constraint rows). x, y device; x is not modified.
+ * Both aprods follow the range rule above: float-pair kernels when the
+ * rescaled input is within [2^-60, 2^60), FP64 kernels otherwise. */
 int gsr_aprod1(gsr_system* sys, const double* x, double* y, void* stream);
-/* Eq. 3 (aprod 2): x[N_unk] += A^T y[n_rows]. x, y device. */
+/* Eq. 3 (aprod 2): x[N_unk] += A^T y[n_eq]. x, y device. */
 int gsr_aprod2(gsr_system* sys, const double* y, double* x, void* stream);
 /* As above on a chosen copy of the values (GSR_VALUES_F32 needs
  * GSR_STORE_F32_PLUS_F64; with it the products use the FP32-rounded A). */
@@ -107,21 +161,21 @@ int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double
 /*
  * Allocation-free aprod 1 (this entry point has no counterpart in the paper):
  * y[n_rows] += A x[N_unk] exactly as gsr_aprod1, for callers that must not
- * allocate device memory when they call it - a host loop being captured into a
- * CUDA graph (allocation cannot be captured), a process whose device memory is
- * held by another framework's caching allocator, or a latency-critical loop that
- * cannot absorb the synchronisation cudaMalloc/cudaFree imply. It calls no
- * cudaMalloc, cudaFree or other allocating routine and uses none of the
- * system's scratch: the float-pair copy of x that the product reads is staged in
- * a fixed device array compiled into the library (GSR_NOALLOC_MAX_UNK float
- * pairs = 8 MiB, held by every GPU that loads the library until the process
- * exits). Systems with N_unk > GSR_NOALLOC_MAX_UNK get GSR_E_UNSUPPORTED.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture begins.
- * Every call on a device shares the one array, and each call rewrites the part
- * it reads (nothing in it needs to start at zero), so calls that overlap on the
- * GPU - on different streams, or for different systems on the same device -
- * race and must be serialised by the caller. x, y device; stream as above.
+ * allocate device memory when they call it - a process whose device memory is
+ * already taken by another framework's caching allocator, or a latency-critical
+ * loop that cannot absorb the device-wide synchronisation cudaMalloc/cudaFree
+ * imply. It calls no cudaMalloc, cudaFree or other allocating routine and uses
+ * none of the system's scratch: the float-pair copy of x that the product reads
+ * is staged in a fixed device array compiled into the library
+ * (GSR_NOALLOC_MAX_UNK float pairs = 8 MiB, plus one 8-byte range flag, held by
+ * every GPU that loads the library until the process exits). Systems with
+ * N_unk > GSR_NOALLOC_MAX_UNK get GSR_E_UNSUPPORTED. The first call on a device
+ * looks up the array's device address (with that device current); make that
+ * first call before any stream capture begins. Every call on a device shares
+ * the one array, and each call rewrites the part it reads (nothing in it needs
+ * to start at zero), so calls that overlap on the GPU - on different streams,
+ * or for different systems on the same device - race and must be serialised
+ * by the caller. x, y device; stream as above.
  */
 #define GSR_NOALLOC_MAX_UNK 1048576
 int gsr_aprod1_noalloc(gsr_system* sys, const double* x, double* y, void* stream);
@@ -142,6 +196,16 @@ typedef struct {
   int32_t mixed_switch_itn;  /* MIXED: iterations of the FP32-values phase (0 = auto) */
   int32_t profile;           /* 1: time aprod 1 / aprod 2 / vector kernels with CUDA
                                 events recorded inside the iteration graph */
+  /* Covariances of chosen pairs of unknowns (Sec. 2.2, Eq. 4). Every
+   * iteration adds d_k[j1] d_k[j2] for each pair, d_k = w_k / rho_k being the
+   * direction whose squares make the variance estimate (Eq. 4's per-iteration
+   * factor is read as 1: the paper does not define it); the result is
+   * de-preconditioned, cov = d_j1 d_j2 sum_k. A pair (j, j) gives var[j].
+   * Index pairs outside [0, N_unk): GSR_E_INDEX. Single right-hand side and
+   * precision F64 only (MIXED computes them in its FP32 phase, like var). */
+  int64_t n_cov;             /* number of pairs (0: none) */
+  const int64_t* cov_pairs;  /* device [n_cov][2]: (j1, j2) */
+  double* cov;               /* device [n_cov] out */
 } gsr_lsqr_opts;
 
 typedef struct {
@@ -156,15 +220,23 @@ typedef struct {
 } gsr_lsqr_result;
 
 /* Fill opts with defaults: atol = btol = 1e-12, conlim = 1e12, itnlim = 0
- * (meaning 20*N_unk), COLNORM, F64, no outputs. */
+ * (meaning 20*N_unk), COLNORM, F64, no outputs (no variance, no covariances). */
 void gsr_lsqr_default_opts(gsr_lsqr_opts* opts);
 
 /*
  * Solve min ||A x - b||_2 by LSQR on A D (D from opts.precond), returning the
- * de-preconditioned x = D z (Sec. 2, solver steps 2-5). b [n_rows] and x
- * [N_unk] are device pointers. Blocks until the result is final (one host
+ * de-preconditioned x = D z (Sec. 2, solver steps 2-5). b [n_eq] (observation
+ * rows, then constraint rows) and x [N_unk] are device pointers. The stopping
+ * tests are those of the preconditioned system the loop solves: ||A D||, and
+ * the norm of its iterate z; res.xnorm reports ||x||. Blocks until the result is final (one host
  * read of the stopping flag every few iterations). Reaching itnlim returns
  * GSR_OK with istop = 7.
+ * Errors: GSR_E_NONFINITE for a NaN/Inf in b; GSR_E_ARG for a user scale that
+ * is not positive and finite; GSR_E_UNSUPPORTED when gsr_create had to give
+ * rows different exponents (a row rescaling would change the least-squares
+ * problem, and it is not folded into D), or when D 2^-g_j leaves [2^-60, 2^60)
+ * for some column (PRECOND_NONE / USER on a column-rescaled system; never
+ * with COLNORM).
  */
 int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_opts* opts,
                    gsr_lsqr_result* res, void* stream);

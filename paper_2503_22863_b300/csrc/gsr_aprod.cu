@@ -64,45 +64,50 @@ __device__ void grid_sum_store(double v, double* part, unsigned int* counter, do
   }
 }
 
-// Exact widening of a float to double with integer operations only (no FP64
-// pipe). Subnormal floats (|f| < 2^-126) become zero.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  if (e == 0u) return __hiloint2double((int)s, 0);
-  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
-  return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
-}
 // x += hi + lo as two L2 reductions (no FP64 arithmetic on the SM).
 __device__ __forceinline__ void red_ff(double* x, ff a) {
-  if (a.h != 0.0f) atomicAdd(x, f2d_bits(a.h));
-  if (a.l != 0.0f) atomicAdd(x, f2d_bits(a.l));
+  if (a.h != 0.0f) atomicAdd(x, f2d_exact(a.h));
+  if (a.l != 0.0f) atomicAdd(x, f2d_exact(a.l));
 }
 
 // ---------------------------------------------------------------------------
 // Element conversions (only at the edges of the C ABI and of a solve).
 // ---------------------------------------------------------------------------
+// out = +-2^-cexp[j] scale[j] x[j] as float pairs (the rescaled input of a
+// product); an entry outside the vector band sets *guard.
 __global__ void k_to_ff(const double* __restrict__ x, const double* __restrict__ scale,
+                        const int16_t* __restrict__ cexp, int neg, double* guard,
                         float2* __restrict__ out, int64_t n) {
+  bool out_of_band = false;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double v = x[j];
     if (scale) v *= scale[j];
+    if (cexp) v = ldexp(v, -(int)cexp[j]);
+    if (neg) v = -v;
+    if (!vec_in_band(v)) out_of_band = true;
     ff f = ff_from_double(v);
     out[j] = make_float2(f.h, f.l);
   }
+  if (guard && out_of_band) *guard = 1.0;
 }
 
-// y (double) -> pairs in row order and in knot order.
+// y (double) -> 2^-e_i y_i as pairs in row order and in knot order; an entry
+// outside the vector band sets *guard.
 __global__ void k_to_ff_knot(Layout L, const double* __restrict__ y, float2* __restrict__ y_ff,
-                             float2* __restrict__ y_knot) {
+                             float2* __restrict__ y_knot, double* guard) {
+  bool out_of_band = false;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const ff f = ff_from_double(y[r]);
-    const float2 v = make_float2(f.h, f.l);
-    y_ff[r] = v;
-    y_knot[L.pos[r]] = v;
+    double v = y[r];
+    if (L.row_exp) v = ldexp(v, -(int)L.row_exp[r]);
+    if (!vec_in_band(v)) out_of_band = true;
+    const ff f = ff_from_double(v);
+    const float2 w = make_float2(f.h, f.l);
+    y_ff[r] = w;
+    y_knot[L.pos[r]] = w;
   }
+  if (guard && out_of_band) *guard = 1.0;
 }
 
 // X3[s*12 + a*4 + j] = x[att_base + a*K + s + j]: the 12 attitude unknowns a
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(NP * 64, 1)
         break;
       }
     if (!got) {
-      if (lane == 0) atomicExch(L.err, GSR_E_TIMEOUT);
+      if (lane == 0) set_error(L.err, GSR_E_TIMEOUT);
       ok = false;
       break;
     }
@@ -318,7 +323,9 @@ __global__ void __launch_bounds__(NP * 64, 1)
         if (y_knot) y_knot[ps] = make_float2(yn.h, yn.l);
       }
     } else {
-      const double yn = __fma_rn(coef, yd, ff_to_double(acc));
+      double a = ff_to_double(acc);
+      if (L.row_exp && live) a = ldexp(a, -(int)L.row_exp[row]);
+      const double yn = __fma_rn(coef, yd, a);
       if (live) {
         static_cast<double*>(yv)[row] = yn;
         nrm_d = __fma_rn(yn, yn, nrm_d);
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
         break;
       }
     if (!__syncthreads_and(got)) {
-      if (threadIdx.x == 0) atomicExch(L.err, GSR_E_TIMEOUT);
+      if (threadIdx.x == 0) set_error(L.err, GSR_E_TIMEOUT);
       ok = false;
       break;
     }
@@ -638,7 +645,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
     // every thread is done with buffer b before a copy into it is issued
     __syncthreads();
   }
-  if (!cas_ok) atomicExch(L.err, GSR_E_TIMEOUT);
+  if (!cas_ok) set_error(L.err, GSR_E_TIMEOUT);
   if (!ok) {
     // let the copies still in flight land before the block exits (bounded)
     for (int q = 0; q < NBUF; ++q)
@@ -745,6 +752,96 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
 }
 
 // ---------------------------------------------------------------------------
+// FP64 products for inputs outside the float-pair band (and for systems whose
+// rescaled coefficients are too spread for it). One thread per row, the
+// coefficient of the stored record widened exactly and scaled back by
+// 2^-(e_i + g_j), products and sums in FP64 (aprod 2 adds into x with FP64 L2
+// atomics). They run only when *guard != 0 (guard null: always), so that the
+// choice between them and the float-pair kernels is made on the device.
+// ---------------------------------------------------------------------------
+template <bool F32>
+__device__ __forceinline__ int64_t rec_col(const Layout& L, const unsigned char* rec, int t,
+                                           int ri) {
+  using R = Rec<F32>;
+  if (t < 5) return 5 * (int64_t)reinterpret_cast<const int*>(rec + R::STAR)[ri] + t;
+  if (t < 17)
+    return L.att_base + ((t - 5) >> 2) * L.n_knots +
+           reinterpret_cast<const int*>(rec + R::ATT_S)[ri] + ((t - 5) & 3);
+  if (t < 23)
+    return L.instr_base +
+           reinterpret_cast<const unsigned short*>(rec + R::INSTR_I + (t - 17) * 128)[ri];
+  return L.glob_col;
+}
+
+// Original coefficient A_it (from the rescaled stored value) and its column.
+template <bool F32>
+__device__ __forceinline__ double rec_coef_f64(const Layout& L, const unsigned char* rec, int t,
+                                               int ri, int e, int64_t col) {
+  const ff v = rec_val1<F32>(rec, t, ri);
+  double a = __dadd_rn((double)v.h, (double)v.l);
+  const int sh = e + (L.col_exp ? (int)L.col_exp[col] : 0);
+  return sh ? ldexp(a, -sh) : a;
+}
+
+// k right-hand sides interleaved (x[col * k + j], y[row * k + j]); k = 1 for
+// the single-vector form.
+template <bool F32>
+__global__ void k_aprod1_f64(Layout L, const double* __restrict__ x, int k, int neg,
+                             double* __restrict__ y, const double* guard) {
+  if (guard && *guard == 0.0) return;
+  using R = Rec<F32>;
+  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
+  const int nt = L.n_glob == 1 ? NSLOT : NSLOT - 1;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < L.n_rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned char* rec = recs + (row / REC_ROWS) * R::BYTES;
+    const int ri = (int)(row % REC_ROWS);
+    const int e = L.row_exp ? (int)L.row_exp[row] : 0;
+    for (int j = 0; j < k; ++j) {
+      double acc = 0.0;
+      for (int t = 0; t < nt; ++t) {
+        const int64_t col = rec_col<F32>(L, rec, t, ri);
+        acc = __fma_rn(rec_coef_f64<F32>(L, rec, t, ri, e, col), x[col * k + j], acc);
+      }
+      y[row * k + j] += neg ? -acc : acc;
+    }
+  }
+}
+
+template <bool F32>
+__global__ void k_aprod2_f64(Layout L, const double* __restrict__ y, int k,
+                             double* __restrict__ x, const double* guard) {
+  if (guard && *guard == 0.0) return;
+  using R = Rec<F32>;
+  const unsigned char* recs = F32 ? L.rec_f32 : L.rec_ff;
+  const int nt = L.n_glob == 1 ? NSLOT : NSLOT - 1;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < L.n_rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned char* rec = recs + (row / REC_ROWS) * R::BYTES;
+    const int ri = (int)(row % REC_ROWS);
+    const int e = L.row_exp ? (int)L.row_exp[row] : 0;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t col = rec_col<F32>(L, rec, t, ri);
+      const double a = rec_coef_f64<F32>(L, rec, t, ri, e, col);
+      for (int j = 0; j < k; ++j) {
+        const double yi = y[row * k + j];
+        if (yi != 0.0) atomicAdd(x + col * k + j, __dmul_rn(a, yi));
+      }
+    }
+  }
+}
+
+// x += 2^-g_j z_j (the column exponents of a rescaled aprod 2), unless *guard.
+__global__ void k_add_rescaled(int64_t n, const double* __restrict__ z,
+                               const int16_t* __restrict__ cexp, double* __restrict__ x,
+                               const double* guard) {
+  if (guard && *guard != 0.0) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    x[j] += ldexp(z[j], -(int)cexp[j]);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 constexpr int A1_NP = 6;                    // warp pairs per aprod 1 block (one block per SM)
@@ -793,35 +890,21 @@ int set_kernel_attributes() {
   return cuda_status(e);
 }
 
-int launch_to_ff(const double* x, const double* scale, float2* out, int64_t n, cudaStream_t st) {
+int launch_to_ff(const double* x, const double* scale, const int16_t* cexp, int neg,
+                 double* guard, float2* out, int64_t n, cudaStream_t st) {
   if (n <= 0) return GSR_OK;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 148 * 8) blocks = 148 * 8;
-  k_to_ff<<<blocks, 256, 0, st>>>(x, scale, out, n);
-  return cuda_status(cudaGetLastError());
-}
-
-__global__ void k_to_ff_neg(const double* __restrict__ x, float2* __restrict__ out, int64_t n) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const ff f = ff_from_double(-x[j]);
-    out[j] = make_float2(f.h, f.l);
-  }
-}
-
-int launch_to_ff_neg(const double* x, float2* out, int64_t n, cudaStream_t st) {
-  if (n <= 0) return GSR_OK;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
-  k_to_ff_neg<<<blocks, 256, 0, st>>>(x, out, n);
+  k_to_ff<<<blocks, 256, 0, st>>>(x, scale, cexp, neg, guard, out, n);
   return cuda_status(cudaGetLastError());
 }
 
 int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
-                      cudaStream_t st) {
+                      double* guard, cudaStream_t st) {
   if (sys->L.n_rows <= 0) return GSR_OK;
   int blocks = (int)((sys->L.n_rows + 255) / 256);
   if (blocks > sys->num_sms * 8) blocks = sys->num_sms * 8;
-  k_to_ff_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_ff, y_knot);
+  k_to_ff_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_ff, y_knot, guard);
   return cuda_status(cudaGetLastError());
 }
 
@@ -882,9 +965,9 @@ int launch_aprod1(gsr_system* sys, int which_values, const float2* x_ff, double*
 }
 
 int launch_aprod1_x3(gsr_system* sys, int which_values, const float2* x_ff, double* y,
-                     cudaStream_t st) {
+                     const double* stop, cudaStream_t st) {
   return launch_aprod1_t<false, true>(sys, which_values, x_ff, y, nullptr, 1.0, nullptr, nullptr,
-                                      nullptr, st);
+                                      stop, st);
 }
 
 int launch_aprod1_ff(gsr_system* sys, int which_values, const float2* x_ff, float2* y,
@@ -933,6 +1016,85 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
   if (cudaEventRecord(sys->ev_join, sys->side) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(st, sys->ev_join, 0) != cudaSuccess) return GSR_E_CUDA;
   return GSR_OK;
+}
+
+int launch_aprod1_f64(gsr_system* sys, int which_values, const double* x, int k, int neg,
+                      double* y, const double* guard, cudaStream_t st) {
+  const Layout& L = sys->L;
+  if (L.n_rows <= 0) return GSR_OK;
+  const int blocks = (int)std::min<int64_t>((L.n_rows + 255) / 256, (int64_t)sys->num_sms * 8);
+  if (which_values == GSR_VALUES_F32)
+    k_aprod1_f64<true><<<blocks, 256, 0, st>>>(L, x, k, neg, y, guard);
+  else
+    k_aprod1_f64<false><<<blocks, 256, 0, st>>>(L, x, k, neg, y, guard);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_aprod2_f64(gsr_system* sys, int which_values, const double* y, int k, double* x,
+                      const double* guard, cudaStream_t st) {
+  const Layout& L = sys->L;
+  if (L.n_rows <= 0) return GSR_OK;
+  const int blocks = (int)std::min<int64_t>((L.n_rows + 255) / 256, (int64_t)sys->num_sms * 8);
+  if (which_values == GSR_VALUES_F32)
+    k_aprod2_f64<true><<<blocks, 256, 0, st>>>(L, y, k, x, guard);
+  else
+    k_aprod2_f64<false><<<blocks, 256, 0, st>>>(L, y, k, x, guard);
+  return cuda_status(cudaGetLastError());
+}
+
+// The observation rows of a direct aprod 1 (float-pair kernels or FP64).
+static int aprod1_direct_obs(gsr_system* sys, int which_values, const double* x, int neg,
+                             double* y, cudaStream_t st) {
+  const Layout& L = sys->L;
+  if (L.n_rows <= 0) return GSR_OK;
+  if (sys->wide) return launch_aprod1_f64(sys, which_values, x, 1, neg, y, nullptr, st);
+  double* guard = sys->S.guard;
+  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  int rc = launch_to_ff(x, nullptr, L.col_exp, neg, guard, sys->S.x_ff, L.n_unk, st);
+  if (rc != GSR_OK) return rc;
+  rc = launch_att_x3(sys, sys->S.x_ff, guard, st);
+  if (rc != GSR_OK) return rc;
+  rc = launch_aprod1_x3(sys, which_values, sys->S.x_ff, y, guard, st);
+  if (rc != GSR_OK) return rc;
+  return launch_aprod1_f64(sys, which_values, x, 1, neg, y, guard, st);
+}
+
+int aprod1_direct(gsr_system* sys, int which_values, const double* x, int neg, double* y,
+                  cudaStream_t st) {
+  const int rc = aprod1_direct_obs(sys, which_values, x, neg, y, st);
+  if (rc != GSR_OK) return rc;
+  return con_aprod1_direct(sys, x, neg, y, st);  // the constraint rows (FP64)
+}
+
+// The observation rows of a direct aprod 2.
+static int aprod2_direct_obs(gsr_system* sys, int which_values, const double* y, double* x,
+                             cudaStream_t st) {
+  const Layout& L = sys->L;
+  if (L.n_rows <= 0) return GSR_OK;
+  if (sys->wide) return launch_aprod2_f64(sys, which_values, y, 1, x, nullptr, st);
+  double* guard = sys->S.guard;
+  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  int rc = launch_to_ff_knot(sys, y, sys->S.y_ff, sys->S.y_knot, guard, st);
+  if (rc != GSR_OK) return rc;
+  double* acc = L.col_exp ? sys->S.zx : x;
+  if (L.col_exp &&
+      cudaMemsetAsync(sys->S.zx, 0, (size_t)L.n_unk * sizeof(double), st) != cudaSuccess)
+    return GSR_E_CUDA;
+  rc = launch_aprod2(sys, which_values, sys->S.y_ff, sys->S.y_knot, acc, guard, st);
+  if (rc != GSR_OK) return rc;
+  if (L.col_exp) {
+    const int blocks = (int)std::min<int64_t>((L.n_unk + 255) / 256, (int64_t)sys->num_sms * 8);
+    k_add_rescaled<<<blocks, 256, 0, st>>>(L.n_unk, sys->S.zx, L.col_exp, x, guard);
+    if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  }
+  return launch_aprod2_f64(sys, which_values, y, 1, x, guard, st);
+}
+
+int aprod2_direct(gsr_system* sys, int which_values, const double* y, double* x,
+                  cudaStream_t st) {
+  const int rc = aprod2_direct_obs(sys, which_values, y, x, st);
+  if (rc != GSR_OK) return rc;
+  return con_aprod2_direct(sys, y, x, st);
 }
 
 }  // namespace gsr

@@ -13,6 +13,7 @@
 // pairs) does not fit one block's shared memory, so blocks split the
 // right-hand sides into chunks of KC (a tuning parameter).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -23,16 +24,9 @@ namespace gsr {
 
 namespace {
 
-__device__ __forceinline__ double f2d_bits_b(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  if (e == 0u) return __hiloint2double((int)s, 0);
-  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
-  return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
-}
 __device__ __forceinline__ void red_ff_b(double* x, ff a) {
-  if (a.h != 0.0f) atomicAdd(x, f2d_bits_b(a.h));
-  if (a.l != 0.0f) atomicAdd(x, f2d_bits_b(a.l));
+  if (a.h != 0.0f) atomicAdd(x, f2d_exact(a.h));
+  if (a.l != 0.0f) atomicAdd(x, f2d_exact(a.l));
 }
 
 // Record accessors for row r_in (0..63) of a record (L1/L2-cached loads; the
@@ -464,40 +458,66 @@ __global__ void __launch_bounds__(256) k_aprod2_instr_csc(Layout L, const int64_
 // ---------------------------------------------------------------------------
 // Conversions between the caller layout [n][k] (double) and [n][KP] pairs.
 // ---------------------------------------------------------------------------
+// in [n][k] -> 2^-cexp[i] in as pairs [n][KP] (padding lanes 0); an entry
+// outside the vector band sets *guard.
 __global__ void k_pack_ff(const double* __restrict__ in, int k, int KP, int64_t n,
+                          const int16_t* __restrict__ cexp, double* guard,
                           float2* __restrict__ out) {
+  bool out_of_band = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / KP;
     const int j = (int)(e % KP);
-    const ff f = ff_from_double(j < k ? in[i * k + j] : 0.0);
+    double v = j < k ? in[i * k + j] : 0.0;
+    if (cexp) v = ldexp(v, -(int)cexp[i]);
+    if (!vec_in_band(v)) out_of_band = true;
+    const ff f = ff_from_double(v);
     out[e] = make_float2(f.h, f.l);
   }
+  if (guard && out_of_band) *guard = 1.0;
 }
+// Y [n_rows][k] -> 2^-e_i Y as pairs in row order and knot order.
 __global__ void k_pack_ff_knot(Layout L, const double* __restrict__ in, int k, int KP,
-                               float2* __restrict__ out, float2* __restrict__ outk) {
+                               double* guard, float2* __restrict__ out,
+                               float2* __restrict__ outk) {
+  bool out_of_band = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.n_rows * KP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / KP;
     const int j = (int)(e % KP);
-    const ff f = ff_from_double(j < k ? in[i * k + j] : 0.0);
+    double v = j < k ? in[i * k + j] : 0.0;
+    if (L.row_exp) v = ldexp(v, -(int)L.row_exp[i]);
+    if (!vec_in_band(v)) out_of_band = true;
+    const ff f = ff_from_double(v);
     out[e] = make_float2(f.h, f.l);
     outk[(int64_t)L.pos[i] * KP + j] = make_float2(f.h, f.l);
   }
+  if (guard && out_of_band) *guard = 1.0;
 }
-__global__ void k_unpack_ff(const float2* __restrict__ in, int k, int KP, int64_t n,
-                            double* __restrict__ out) {
+// Y[n][k] += 2^-e_i U (the pairs of a batched aprod 1), unless *guard.
+__global__ void k_unpack_add(const float2* __restrict__ in, int k, int KP, int64_t n,
+                             const int16_t* __restrict__ rexp, const double* guard,
+                             double* __restrict__ out) {
+  if (guard && *guard != 0.0) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = in[(e / k) * KP + e % k];
-    out[e] = ff_to_double(ff{v.x, v.y});
+    const int64_t i = e / k;
+    const float2 v = in[i * KP + e % k];
+    const double a = ff_to_double(ff{v.x, v.y});
+    out[e] += rexp ? ldexp(a, -(int)rexp[i]) : a;
   }
 }
+// X[n][k] += 2^-g_i Z (a batched aprod 2 accumulator), unless *guard.
 __global__ void k_add_cols(const double* __restrict__ in, int k, int KP, int64_t n,
+                           const int16_t* __restrict__ cexp, const double* guard,
                            double* __restrict__ out) {
+  if (guard && *guard != 0.0) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
-       e += (int64_t)gridDim.x * blockDim.x)
-    out[e] += in[(e / k) * KP + e % k];
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    const double a = in[i * KP + e % k];
+    out[e] += cexp ? ldexp(a, -(int)cexp[i]) : a;
+  }
 }
 __global__ void k_zero_d(double* __restrict__ a, int64_t n, const double* stop) {
   if (stop && *stop != 0.0) return;
@@ -515,21 +535,49 @@ __global__ void k_zero_d(double* __restrict__ a, int64_t n, const double* stop) 
 enum BS {
   B_ALPHA = 0, B_BETA, B_RHOBAR, B_PHIBAR, B_ANORM2, B_DDNORM, B_BNORM, B_RHO, B_C, B_T1, B_T2,
   B_RNORM, B_ARNORM, B_ACOND, B_XNORM, B_ITN, B_ISTOP, B_DONE, B_UNORM2, B_COEF, B_XREF2,
+  B_BEXP,  // right-hand side j is solved as 2^-s_j b_j (largest entry in [1, 2))
   B_COUNT
 };
 enum BG { G_ALLDONE = 0, G_ATOL, G_BTOL, G_CTOL, G_ITNLIM, G_K, G_ITER, G_COUNT };
 
+// Largest binary exponent of each right-hand side into mx[j] (atomicMax, mx
+// preset very negative); a NaN or Inf sets *bad. LSQR is invariant under
+// b_j -> 2^-s b_j, so every right-hand side is solved with its largest entry
+// in [1, 2) and its x and residual norms are scaled back.
+template <int KP>
+__global__ void __launch_bounds__(256) k_maxexp_b(const double* __restrict__ B, int k, int64_t n,
+                                                  int* mx, double* bad) {
+  const int j = (int)(threadIdx.x % KP);
+  int m = INT_MIN;
+  bool nonfinite = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (j >= k) continue;
+    const double v = B[(e / KP) * k + j];
+    if (!isfinite(v)) nonfinite = true;
+    else if (v != 0.0) m = max(m, ilogb(v));
+  }
+#pragma unroll
+  for (int o = 16; o >= KP; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) < KP && j < k && m != INT_MIN) atomicMax(mx + j, m);
+  if (nonfinite) *bad = 1.0;
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256) k_init_b(Layout L, const double* __restrict__ B, int k,
-                                                float2* __restrict__ U, float2* __restrict__ Uk,
-                                                double* sc, double* part, unsigned int* counter) {
+                                                const int* bexp, float2* __restrict__ U,
+                                                float2* __restrict__ Uk, double* sc, double* part,
+                                                unsigned int* counter) {
   __shared__ double tot[32];
   double s2 = 0.0;
+  const int jt = (int)(threadIdx.x % KP);
+  const int sb = jt < k && bexp[jt] > -4000 ? bexp[jt] : 0;
+  if (blockIdx.x == 0 && threadIdx.x < KP) sc[B_BEXP * KP + jt] = sb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.n_rows * KP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / KP;
     const int j = (int)(e % KP);
-    const double v = j < k ? B[i * k + j] : 0.0;
+    const double v = j < k ? ldexp(B[i * k + j], -sb) : 0.0;
     const ff f = ff_from_double(v);
     U[e] = make_float2(f.h, f.l);
     Uk[(int64_t)L.pos[i] * KP + j] = make_float2(f.h, f.l);
@@ -638,20 +686,23 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
                                                  float2* __restrict__ V, float2* __restrict__ W,
                                                  float2* __restrict__ XZ,
                                                  float2* __restrict__ Vff,
-                                                 const double* __restrict__ xref, double* sc,
+                                                 const double* __restrict__ xref,
+                                                 const int16_t* __restrict__ cexp, double* sc,
                                                  double* part, unsigned int* counter, int first,
                                                  double* err_hist) {
-  __shared__ double tot[3 * 32];
+  __shared__ double tot[4 * 32];
   double* g = sc + B_COUNT * KP;
   if (g[G_ALLDONE] != 0.0) return;
   const int j = threadIdx.x % KP;
+  const int sb = (int)sc[B_BEXP * KP + j];
+  double x2d = 0.0;
   const bool frozen = sc[B_DONE * KP + j] != 0.0 || j >= (int)g[G_K];
   const double alpha = sc[B_ALPHA * KP + j];
   const ff ia = ff_from_double(alpha > 0.0 ? 1.0 / alpha : 0.0);
   const ff irho = ff_from_double(first ? 1.0 : 1.0 / sc[B_RHO * KP + j]);
   const ff t1 = ff_from_double(first ? 0.0 : sc[B_T1 * KP + j]);
   const ff t2 = ff_from_double(first ? 0.0 : sc[B_T2 * KP + j]);
-  ff dk2f = ff_zero(), x2f = ff_zero();  // ||d_k||^2, ||x||^2
+  ff dk2f = ff_zero(), x2f = ff_zero(), z2f = ff_zero();  // ||d_k||^2, ||x||^2, ||z||^2
   double e2 = 0.0;                       // ||x - x_ref||^2
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < n * KP;
@@ -695,6 +746,7 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
           dk2f = ff_add(dk2f, ff_mul(dk, dk));
           const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
           XZ[e] = make_float2(xn.h, xn.l);
+          z2f = ff_add(z2f, ff_mul(xn, xn));
           const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
           W[e] = make_float2(wn.h, wn.l);
           xv = ff_norm(ff_mul(dj, xn));
@@ -703,15 +755,23 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
         const ff f = ff_norm(ff_mul(dj, vn));
         Vff[e] = make_float2(f.h, f.l);
       }
-      x2f = ff_add(x2f, ff_mul(xv, xv));
+      // x = 2^g D' z: in FP64 when the system has column exponents
+      double xd = 0.0;
+      if (cexp) {
+        xd = ldexp(ff_to_double(xv), (int)cexp[e / KP]);
+        x2d = __fma_rn(xd, xd, x2d);
+      } else {
+        x2f = ff_add(x2f, ff_mul(xv, xv));
+        if (xref) xd = ff_to_double(xv);
+      }
       if (xref) {
-        const double ex = ff_to_double(xv) - xref[e];
+        const double ex = ldexp(xd, sb) - xref[e];
         e2 = __fma_rn(ex, ex, e2);
       }
     }
   }
-  double acc[3] = {ff_to_double(dk2f), ff_to_double(x2f), e2};
-  if (!grid_sum_kv<KP, 3>(acc, part, counter, tot)) return;
+  double acc[4] = {ff_to_double(dk2f), ff_to_double(x2f) + x2d, e2, ff_to_double(z2f)};
+  if (!grid_sum_kv<KP, 4>(acc, part, counter, tot)) return;
   const int K = (int)g[G_K];
   if (first) {
     if (threadIdx.x == 0) {
@@ -747,8 +807,10 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
       const double test1 = rnorm / bnorm;
       const double test2 = (anorm * rnorm > 0.0) ? arnorm / (anorm * rnorm) : 0.0;
       const double test3 = 1.0 / acond;
-      const double t1n = test1 / (1.0 + anorm * xnorm / bnorm);
-      const double rtol = btol + atol * anorm * xnorm / bnorm;
+      // tests on the preconditioned system: ||A D|| and the norm of its iterate z
+      const double znorm = sqrt(tot[96 + jj]);
+      const double t1n = test1 / (1.0 + anorm * znorm / bnorm);
+      const double rtol = btol + atol * anorm * znorm / bnorm;
       int istop = 0;
       if (itn >= g[G_ITNLIM]) istop = 7;
       if (1.0 + test3 <= 1.0) istop = 6;
@@ -773,19 +835,23 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
   }
 }
 
-// x_j = D z_j into the caller layout [n][k].
+// x_j = 2^s_j D z_j into the caller layout [n][k].
 __global__ void k_finish_b(int64_t n, int k, int KP, const double* __restrict__ d,
-                           const float2* __restrict__ XZ, double* __restrict__ x) {
+                           const float2* __restrict__ XZ, const double* __restrict__ sc,
+                           double* __restrict__ x) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / k;
-    const float2 z = XZ[i * KP + e % k];
-    x[e] = d[i] * ff_to_double(ff{z.x, z.y});
+    const int j = (int)(e % k);
+    const float2 z = XZ[i * KP + j];
+    x[e] = d[i] * ldexp(ff_to_double(ff{z.x, z.y}), (int)sc[B_BEXP * KP + j]);
   }
 }
+// D (FP64) and the pairs of D' = 2^-g D; *bad as for the single solve (2: a
+// scale not positive and finite, 1: D' outside the vector band).
 __global__ void k_scale_b(int64_t n, int mode, const double* __restrict__ colnorm,
-                          const double* __restrict__ user, double* __restrict__ dsc,
-                          float2* __restrict__ dsc_ff) {
+                          const double* __restrict__ user, const int16_t* __restrict__ cexp,
+                          double* __restrict__ dsc, float2* __restrict__ dsc_ff, double* bad) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double s = 1.0;
@@ -796,7 +862,10 @@ __global__ void k_scale_b(int64_t n, int mode, const double* __restrict__ colnor
       s = user[j];
     }
     dsc[j] = s;
-    const ff f = ff_from_double(s);
+    const double sp = cexp ? ldexp(s, -(int)cexp[j]) : s;
+    if (!(s > 0.0) || !isfinite(s)) *bad = 2.0;
+    else if (!vec_in_band(sp)) *bad = 1.0;
+    const ff f = ff_from_double(sp);
     dsc_ff[j] = make_float2(f.h, f.l);
   }
 }
@@ -1054,7 +1123,8 @@ static int enqueue_b(gsr_system* s, BatchWork* w, const double* xref, double* er
   if (rc != GSR_OK) return rc;
   k_vec_a_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->Z, w->V, w->sc, w->part, w->count + 1, first);
   k_vec_b_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->V, w->W, w->XZ, w->Vff, first ? nullptr : xref,
-                                    w->sc, w->part, w->count + 2, first, first ? nullptr : err_dev);
+                                    s->L.col_exp, w->sc, w->part, w->count + 2, first,
+                                    first ? nullptr : err_dev);
   return cuda_status(cudaGetLastError());
 }
 static int enqueue_iter_b(gsr_system* s, BatchWork* w, const double* xref, double* err_dev,
@@ -1065,8 +1135,8 @@ template <int KP>
 static int init_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
                   cudaStream_t st) {
   const int64_t rb = std::min<int64_t>((s->L.n_rows * KP + 255) / 256, (int64_t)s->num_sms * 8);
-  k_init_b<KP><<<(int)std::max<int64_t>(rb, 1), 256, 0, st>>>(s->L, B, k, w->U, w->Uk, w->sc,
-                                                              w->part, w->count + 3);
+  k_init_b<KP><<<(int)std::max<int64_t>(rb, 1), 256, 0, st>>>(s->L, B, k, s->S.iexp, w->U, w->Uk,
+                                                              w->sc, w->part, w->count + 3);
   if (xref) {
     const int vb = (int)std::min<int64_t>((s->L.n_unk * KP + 255) / 256, (int64_t)s->num_sms * 8);
     k_xref2_b<KP><<<vb, 256, 0, st>>>(s->L.n_unk, xref, w->sc, w->part, w->count + 4);
@@ -1100,7 +1170,32 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
     if (e == cudaSuccess) e = x;
   };
   const int vb = (int)std::min<int64_t>((m + 255) / 256, (int64_t)s->num_sms * 8);
-  k_scale_b<<<vb, 256, 0, st>>>(m, o->precond, s->colnorm, o->scale, w->D, w->Dff);
+  // column scaling D and the pairs of D' = 2^-g D (checked), exponent of each
+  // right-hand side (and a check that B is finite)
+  C(cudaMemsetAsync(s->S.guard + 1, 0, 3 * sizeof(double), st));
+  C(cudaMemsetAsync(s->S.iexp, 0x80, 32 * sizeof(int), st));
+  k_scale_b<<<vb, 256, 0, st>>>(m, o->precond, s->colnorm, o->scale, s->L.col_exp, w->D, w->Dff,
+                                s->S.guard + 1);
+  {
+    const int rb = (int)std::max<int64_t>(
+        1, std::min<int64_t>((s->L.n_rows * KP + 255) / 256, (int64_t)s->num_sms * 8));
+    switch (KP) {
+      case 1: k_maxexp_b<1><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+      case 2: k_maxexp_b<2><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+      case 4: k_maxexp_b<4><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+      case 8: k_maxexp_b<8><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+      case 16: k_maxexp_b<16><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+      default: k_maxexp_b<32><<<rb, 256, 0, st>>>(B, k, s->L.n_rows, s->S.iexp, s->S.guard + 3); break;
+    }
+    double flags[3] = {0.0, 0.0, 0.0};
+    C(cudaGetLastError());
+    C(cudaMemcpyAsync(flags, s->S.guard + 1, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    C(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) return GSR_E_CUDA;
+    if (flags[0] == 2.0) return GSR_E_ARG;
+    if (flags[0] != 0.0) return GSR_E_UNSUPPORTED;
+    if (flags[2] != 0.0) return GSR_E_NONFINITE;
+  }
   // the autotuner runs once per system and k, on the (so far unused) work vectors
   if (!w->tuned) {
     C(cudaMemsetAsync(w->Vff, 0, m * KP * 8, st));
@@ -1129,7 +1224,7 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
   rc = init_iter_b(s, w, B, k, xref, st);
   if (rc == GSR_OK) rc = enqueue_iter_b(s, w, xref, err_dev, st, 1);
   if (rc != GSR_OK) return rc;
-  int64_t n_launches = 11;
+  int64_t n_launches = 12;
   // iterations: graph of a chunk of iterations, replayed until every RHS stopped
   const int chunk = 4;
   cudaGraph_t graph = nullptr;
@@ -1178,7 +1273,7 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
     if (err_dev) cudaFreeAsync(err_dev, st);
     return rc != GSR_OK ? rc : GSR_E_CUDA;
   }
-  k_finish_b<<<vb, 256, 0, st>>>(m, k, KP, w->D, w->XZ, X);
+  k_finish_b<<<vb, 256, 0, st>>>(m, k, KP, w->D, w->XZ, w->sc, X);
   const int64_t iters = (int64_t)w->hsc[B_COUNT * KP + G_ITER];
   if (o->err_hist && err_dev && iters > 0)
     C(cudaMemcpyAsync(o->err_hist, err_dev, iters * k * 8, cudaMemcpyDeviceToHost, st));
@@ -1190,13 +1285,14 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
   for (int j = 0; j < k; ++j) {
     gsr_lsqr_result& r = res[j];
     std::memset(&r, 0, sizeof(r));
+    const int sb = (int)hs[B_BEXP * KP + j];
     r.istop = (int32_t)hs[B_ISTOP * KP + j];
     r.itn = (int64_t)hs[B_ITN * KP + j];
-    r.rnorm = hs[B_RNORM * KP + j];
-    r.arnorm = hs[B_ARNORM * KP + j];
+    r.rnorm = std::ldexp(hs[B_RNORM * KP + j], sb);
+    r.arnorm = std::ldexp(hs[B_ARNORM * KP + j], sb);
     r.anorm = std::sqrt(hs[B_ANORM2 * KP + j]);
     r.acond = hs[B_ACOND * KP + j];
-    r.xnorm = hs[B_XNORM * KP + j];
+    r.xnorm = std::ldexp(hs[B_XNORM * KP + j], sb);
     r.n_launches = n_launches;
     r.n_timed_itn = iters;
   }
@@ -1213,8 +1309,13 @@ extern "C" {
 int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* stream) {
   if (!sys || k < 1 || k > 32 || (!X && sys->L.n_unk > 0) || (!Y && sys->L.n_rows > 0))
     return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  if (sys->n_con > 0) return GSR_E_UNSUPPORTED;  // constraint rows: single-vector forms only
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (sys->L.n_rows == 0) return GSR_OK;
+  if (sys->wide) return gsr::launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, 0, Y, nullptr, st);
   const int KP = gsr::kpad(k);
   gsr::BatchWork* w = nullptr;
   int rc = gsr::batch_work(sys, KP, &w, st);
@@ -1222,19 +1323,29 @@ int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* s
   const int64_t m = sys->L.n_unk, n = sys->L.n_rows;
   const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
   const int bn = (int)std::min<int64_t>((n * KP + 255) / 256 + 1, sys->num_sms * 8);
-  gsr::k_pack_ff<<<bm, 256, 0, st>>>(X, k, KP, m, w->Vff);
-  gsr::k_pack_ff<<<bn, 256, 0, st>>>(Y, k, KP, n, w->U);
-  rc = gsr::aprod1_b(sys, w, w->Vff, w->U, nullptr, nullptr, nullptr, nullptr, st);
+  double* guard = sys->S.guard;
+  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  // U = A' X' (pairs, from zero), then Y += 2^-e U in FP64
+  if (cudaMemsetAsync(w->U, 0, (size_t)n * KP * sizeof(float2), st) != cudaSuccess)
+    return GSR_E_CUDA;
+  gsr::k_pack_ff<<<bm, 256, 0, st>>>(X, k, KP, m, sys->L.col_exp, guard, w->Vff);
+  rc = gsr::aprod1_b(sys, w, w->Vff, w->U, nullptr, nullptr, nullptr, guard, st);
   if (rc != GSR_OK) return rc;
-  gsr::k_unpack_ff<<<bn, 256, 0, st>>>(w->U, k, KP, n, Y);
-  return gsr::cuda_status(cudaGetLastError());
+  gsr::k_unpack_add<<<bn, 256, 0, st>>>(w->U, k, KP, n, sys->L.row_exp, guard, Y);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  return gsr::launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, 0, Y, guard, st);
 }
 
 int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* stream) {
   if (!sys || k < 1 || k > 32 || (!X && sys->L.n_unk > 0) || (!Y && sys->L.n_rows > 0))
     return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  if (sys->n_con > 0) return GSR_E_UNSUPPORTED;  // constraint rows: single-vector forms only
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (sys->L.n_rows == 0) return GSR_OK;
+  if (sys->wide) return gsr::launch_aprod2_f64(sys, GSR_VALUES_F64, Y, k, X, nullptr, st);
   const int KP = gsr::kpad(k);
   gsr::BatchWork* w = nullptr;
   int rc = gsr::batch_work(sys, KP, &w, st);
@@ -1242,12 +1353,15 @@ int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* s
   const int64_t m = sys->L.n_unk;
   const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
   const int bn = (int)std::min<int64_t>((sys->L.n_rows * KP + 255) / 256 + 1, sys->num_sms * 8);
-  gsr::k_pack_ff_knot<<<bn, 256, 0, st>>>(sys->L, Y, k, KP, w->U, w->Uk);
+  double* guard = sys->S.guard;
+  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  gsr::k_pack_ff_knot<<<bn, 256, 0, st>>>(sys->L, Y, k, KP, guard, w->U, w->Uk);
   gsr::k_zero_d<<<bm, 256, 0, st>>>(w->Z, m * KP, nullptr);
-  rc = gsr::aprod2_b(sys, w, w->U, w->Uk, w->Z, nullptr, st);
+  rc = gsr::aprod2_b(sys, w, w->U, w->Uk, w->Z, guard, st);
   if (rc != GSR_OK) return rc;
-  gsr::k_add_cols<<<bm, 256, 0, st>>>(w->Z, k, KP, m, X);
-  return gsr::cuda_status(cudaGetLastError());
+  gsr::k_add_cols<<<bm, 256, 0, st>>>(w->Z, k, KP, m, sys->L.col_exp, guard, X);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  return gsr::launch_aprod2_f64(sys, GSR_VALUES_F64, Y, k, X, guard, st);
 }
 
 int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
@@ -1256,16 +1370,22 @@ int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
   if ((!B && sys->L.n_rows > 0) || (!X && sys->L.n_unk > 0)) return GSR_E_ARG;
   if (opts->precond < GSR_PRECOND_NONE || opts->precond > GSR_PRECOND_USER) return GSR_E_ARG;
   if (opts->precond == GSR_PRECOND_USER && !opts->scale) return GSR_E_ARG;
-  if (opts->precision != GSR_PREC_F64 || opts->var || opts->rnorm_hist) return GSR_E_UNSUPPORTED;
+  if (opts->precision != GSR_PREC_F64 || opts->var || opts->rnorm_hist || opts->n_cov > 0)
+    return GSR_E_UNSUPPORTED;
   if (opts->err_hist && !opts->x_ref) return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  if (sys->row_scaled) return GSR_E_UNSUPPORTED;  // as for gsr_lsqr_solve
+  if (sys->n_con > 0) return GSR_E_UNSUPPORTED;    // constraint rows: single-vector forms only
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sys->L.n_rows == 0 || sys->L.n_unk == 0) {
     if (X && sys->L.n_unk > 0) cudaMemsetAsync(X, 0, sys->L.n_unk * k * 8, st);
     for (int j = 0; j < k; ++j) std::memset(&res[j], 0, sizeof(res[j]));
     return gsr::cuda_status(cudaStreamSynchronize(st));
   }
-  return gsr::lsqr_batch(sys, k, B, X, opts, res, st);
+  const int rc = gsr::lsqr_batch(sys, k, B, X, opts, res, st);
+  return rc == GSR_OK ? gsr::sticky_error(sys) : rc;
 }
 
 int gsr_batch_tuning(const gsr_system* sys, int* threads, int* tile_rows) {

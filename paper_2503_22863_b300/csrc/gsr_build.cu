@@ -9,6 +9,7 @@
 // block. The column norms ||A_:,j|| (used by the column-scaling preconditioner,
 // Sec. 2 solver step 2) are computed on the device.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -35,7 +36,8 @@ __device__ __forceinline__ void put_indices(unsigned char* rec, int l, int c, in
 }
 
 // Lay out rows [r0, r0+n) of the raw upload into the records and the
-// knot-ordered attitude copy; accumulate the squared column norms.
+// knot-ordered attitude copy, each value rescaled to 2^(e_i + g_j) A_ij when
+// the system has exponents; accumulate the squared column norms of 2^g_j A_ij.
 __global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
                          unsigned char* __restrict__ rec_f32, float2* __restrict__ att_ff,
                          float* __restrict__ att_f32, const double* __restrict__ raw,
@@ -48,34 +50,41 @@ __global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
     const int64_t rec = r / REC_ROWS;
     const int l = (int)((r % REC_ROWS) >> 1), c = (int)(r & 1);
     const int st = star[r], sk = s_knot[r], p = L.pos[r];
+    const int er = L.row_exp ? (int)L.row_exp[r] : 0;
     unsigned char* rf = rec_ff + rec * Rec<false>::BYTES;
     unsigned char* r32 = rec_f32 ? rec_f32 + rec * Rec<true>::BYTES : nullptr;
     put_indices<false>(rf, l, c, st, sk, p, raw_instr + i * 6);
     if (r32) put_indices<true>(r32, l, c, st, sk, p, raw_instr + i * 6);
     for (int t = 0; t < NSLOT; ++t) {
       double v = raw[i * NSLOT + t];
-      if (t == 23 && L.n_glob == 0) v = 0.0;
-      const float h = __double2float_rn(v);
-      const float lo = __double2float_rn(v - (double)h);
-      float* pf = reinterpret_cast<float*>(rf + slot_offset<false>(t) + l * 16);
-      pf[2 * c] = h;
-      pf[2 * c + 1] = lo;
-      if (r32) reinterpret_cast<float*>(r32 + slot_offset<true>(t) + l * 8)[c] = h;
-      int64_t col;
+      int64_t col = -1;
       if (t < 5) {
         col = 5 * (int64_t)st + t;
       } else if (t < 17) {
         const int a = (t - 5) >> 2, jj = (t - 5) & 3;
         col = L.att_base + a * L.n_knots + sk + jj;
-        att_ff[(int64_t)(t - 5) * L.n_rows + p] = make_float2(h, lo);
-        if (att_f32) att_f32[(int64_t)(t - 5) * L.n_rows + p] = h;
       } else if (t < 23) {
         col = L.instr_base + raw_instr[i * 6 + (t - 17)];
-      } else {
-        if (L.n_glob == 0) continue;
+      } else if (L.n_glob == 1) {
         col = L.glob_col;
+      } else {
+        v = 0.0;
       }
-      atomicAdd(c2 + col, v * v);
+      const int ec = (col >= 0 && L.col_exp) ? (int)L.col_exp[col] : 0;
+      const double vs = (er + ec) ? ldexp(v, er + ec) : v;  // exact power-of-two rescaling
+      const float h = __double2float_rn(vs);
+      const float lo = __double2float_rn(vs - (double)h);
+      float* pf = reinterpret_cast<float*>(rf + slot_offset<false>(t) + l * 16);
+      pf[2 * c] = h;
+      pf[2 * c + 1] = lo;
+      if (r32) reinterpret_cast<float*>(r32 + slot_offset<true>(t) + l * 8)[c] = h;
+      if (t >= 5 && t < 17) {
+        att_ff[(int64_t)(t - 5) * L.n_rows + p] = make_float2(h, lo);
+        if (att_f32) att_f32[(int64_t)(t - 5) * L.n_rows + p] = h;
+      }
+      if (col < 0) continue;
+      const double vc = ec ? ldexp(v, ec) : v;
+      atomicAdd(c2 + col, vc * vc);
     }
   }
 }
@@ -91,10 +100,13 @@ __global__ void k_pad_records(Layout L, unsigned char* rec_ff, unsigned char* re
   if (rec_f32) put_indices<true>(rec_f32 + rec * Rec<true>::BYTES, l, c, star, 0, 0, zeros);
 }
 
-__global__ void k_sqrt(double* __restrict__ a, int64_t n) {
+// ||A_:,j|| = 2^-g_j ||2^g_j A_:,j||.
+__global__ void k_sqrt(double* __restrict__ a, const int16_t* __restrict__ cexp, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x)
-    a[j] = sqrt(a[j]);
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double c = sqrt(a[j]);
+    a[j] = cexp ? ldexp(c, -(int)cexp[j]) : c;
+  }
 }
 
 template <typename T>
@@ -113,15 +125,19 @@ int dalloc(T** p, size_t count) {
 void free_system(gsr_system* s) {
   if (!s) return;
   destroy_batch(s);
+  free_constraints(s);
+  delete[] s->colnorm_obs;
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
                   s->att_warp_knot, s->iseg, s->ient_ff, s->ient_f32,
-                  s->ient_key, s->err, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
+                  s->ient_key, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
                   s->dscale, s->dscale_ff, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
                   s->S.count, s->S.x_ff, s->S.x3,
-                  s->S.y_ff, s->S.y_knot, s->instr_count};
+                  s->S.y_ff, s->S.y_knot, s->instr_count, s->row_exp, s->col_exp,
+                  s->S.guard, s->S.iexp, s->S.zx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->host_scal) cudaFreeHost(s->host_scal);
+  if (s->err_host) cudaFreeHost(s->err_host);
   if (s->side) cudaStreamDestroy(s->side);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
@@ -169,6 +185,205 @@ void parallel_for(int64_t n, unsigned nt, F f) {
   for (auto& t : th) t.join();
 }
 
+// ---------------------------------------------------------------------------
+// Exact power-of-two rescaling of the coefficients (host, at creation). The
+// float-pair kernels carry FP32's exponent range; FP64 input may span far more.
+// Scaling row i by 2^e_i and column j by 2^g_j is exact and is undone exactly
+// at the edges (vector conversions, FP64 outputs, the column preconditioner),
+// so it changes no result. Chosen in this order:
+//   1. every nonzero |A_ij| in [2^-40, 2^40): no rescaling at all;
+//   2. column exponents only (column maxima to [1, 2)), if that leaves every
+//      coefficient >= 2^-100;
+//   3. otherwise row and column exponents that fit the binary exponents of the
+//      coefficients in the least-squares sense (alternately subtract each
+//      row's and each column's mean exponent, rounded, until nothing moves;
+//      for A = R A0 C this recovers R and C up to the spread of A0), then
+//      column maxima to [1, 2).
+// A coefficient still below 2^-100 of the largest of its column after that
+// has a spread no diagonal scaling removes (a 2 x 2 minor decides it):
+// GSR_E_UNSUPPORTED. Below 2^-40 the system is "wide": its direct products run
+// the FP64 kernels.
+// ---------------------------------------------------------------------------
+struct Rescale {
+  std::vector<int16_t> row, col;  // empty: all exponents 0
+  bool row_scaled = false, wide = false;
+};
+
+constexpr int NO_EXP = INT32_MIN / 2;
+
+// Column of slot t of row i (or -1 for the absent global slot).
+inline int64_t slot_col(const gsr_dims& d, const int32_t* star, const int32_t* s_knot,
+                        const int32_t* instr, int64_t i, int t) {
+  const int64_t att_base = 5 * d.n_stars, instr_base = att_base + 3 * d.n_knots;
+  if (t < 5) return 5 * (int64_t)star[i] + t;
+  if (t < 17) return att_base + ((t - 5) >> 2) * d.n_knots + s_knot[i] + ((t - 5) & 3);
+  if (t < 23) return instr_base + instr[i * 6 + (t - 17)];
+  return d.n_glob == 1 ? instr_base + d.n_instr : -1;
+}
+
+// Row chunks for nt threads that never split a star (the astrometric columns
+// of a star are then touched by one thread only).
+std::vector<int64_t> star_chunks(const int32_t* star, int64_t n, unsigned nt) {
+  std::vector<int64_t> b(1, 0);
+  for (unsigned k = 1; k < nt; ++k) {
+    int64_t r = std::max(b.back(), (n * (int64_t)k) / nt);
+    while (r > 0 && r < n && star[r] == star[r - 1]) ++r;
+    b.push_back(std::min(r, n));
+  }
+  b.push_back(n);
+  return b;
+}
+
+// Statistics of x_ij = ilogb|A_ij| + e_i + g_j over the nonzero coefficients:
+// per row the sum and count (rsum, rcnt), per column the largest (cmax) or the
+// sum and count (csum, ccnt); returns the smallest x_ij. Null outputs are
+// skipped.
+struct ExpStats {
+  std::vector<int64_t> rsum, csum;
+  std::vector<int32_t> rcnt, ccnt, cmax;
+};
+int scan_exponents(const gsr_dims& d, const double* vals, const int32_t* star,
+                   const int32_t* s_knot, const int32_t* instr, const std::vector<int>& e,
+                   const std::vector<int>& g, unsigned nt, bool rows, bool col_sums,
+                   bool col_max, ExpStats& out) {
+  const int64_t n = d.n_rows, n_unk = (int64_t)g.size();
+  const int64_t sh0 = 5 * d.n_stars, n_sh = n_unk - sh0;  // columns shared between stars
+  const std::vector<int64_t> ch = star_chunks(star, n, nt);
+  const unsigned nc = (unsigned)ch.size() - 1;
+  if (rows) {
+    out.rsum.assign(n, 0);
+    out.rcnt.assign(n, 0);
+  }
+  if (col_sums) {
+    out.csum.assign(n_unk, 0);
+    out.ccnt.assign(n_unk, 0);
+  }
+  if (col_max) out.cmax.assign(n_unk, NO_EXP);
+  std::vector<std::vector<int64_t>> lsum(nc);
+  std::vector<std::vector<int32_t>> lcnt(nc), lmax(nc);
+  std::vector<int> mins(nc, INT32_MAX);
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nc; ++k)
+    th.emplace_back([&, k] {
+      if (col_sums) {
+        lsum[k].assign(n_sh, 0);
+        lcnt[k].assign(n_sh, 0);
+      }
+      if (col_max) lmax[k].assign(n_sh, NO_EXP);
+      int mn = INT32_MAX;
+      for (int64_t i = ch[k]; i < ch[k + 1]; ++i) {
+        int64_t rs = 0;
+        int32_t rc = 0;
+        for (int t = 0; t < NSLOT; ++t) {
+          const double v = vals[i * NSLOT + t];
+          if (v == 0.0) continue;
+          const int64_t c = slot_col(d, star, s_knot, instr, i, t);
+          if (c < 0) continue;
+          const int x = std::ilogb(v) + e[i] + g[c];
+          mn = std::min(mn, x);
+          rs += x;
+          ++rc;
+          const bool own = c < sh0;  // an astrometric column: this thread's alone
+          if (col_sums) {
+            (own ? out.csum[c] : lsum[k][c - sh0]) += x;
+            ++(own ? out.ccnt[c] : lcnt[k][c - sh0]);
+          }
+          if (col_max) {
+            int32_t& m = own ? out.cmax[c] : lmax[k][c - sh0];
+            m = std::max(m, (int32_t)x);
+          }
+        }
+        if (rows) {
+          out.rsum[i] = rs;
+          out.rcnt[i] = rc;
+        }
+      }
+      mins[k] = mn;
+    });
+  for (auto& t : th) t.join();
+  for (unsigned k = 0; k < nc; ++k)
+    for (int64_t c = 0; c < n_sh; ++c) {
+      if (col_sums) {
+        out.csum[sh0 + c] += lsum[k][c];
+        out.ccnt[sh0 + c] += lcnt[k][c];
+      }
+      if (col_max) out.cmax[sh0 + c] = std::max(out.cmax[sh0 + c], lmax[k][c]);
+    }
+  int mn = INT32_MAX;
+  for (int m : mins) mn = std::min(mn, m);
+  return mn;
+}
+
+// round(sum / count) for count > 0
+inline int mean_exp(int64_t sum, int32_t cnt) {
+  return (int)std::llround((double)sum / (double)cnt);
+}
+
+int choose_rescaling(const gsr_dims& d, const double* vals, const int32_t* star,
+                     const int32_t* s_knot, const int32_t* instr, unsigned nt, Rescale& out) {
+  const int64_t n = d.n_rows;
+  const int64_t n_unk = 5 * d.n_stars + 3 * d.n_knots + d.n_instr + d.n_glob;
+  out = Rescale();
+  if (n == 0) return GSR_OK;
+  std::vector<int> e(n, 0), g(n_unk, 0);
+  ExpStats st;
+  const int mn0 = scan_exponents(d, vals, star, s_knot, instr, e, g, nt, false, false, true, st);
+  int mx0 = NO_EXP;
+  for (int v : st.cmax) mx0 = std::max(mx0, v);
+  if (mx0 == NO_EXP || (mn0 >= MAT_BAND_LO && mx0 < MAT_BAND_HI)) return GSR_OK;  // step 1
+  // step 2: column maxima to [1, 2)
+  for (int64_t c = 0; c < n_unk; ++c) g[c] = st.cmax[c] == NO_EXP ? 0 : -st.cmax[c];
+  int mn = scan_exponents(d, vals, star, s_knot, instr, e, g, nt, false, false, false, st);
+  if (mn < MAT_WIDE_LO) {
+    // step 3: least-squares fit of row and column exponents
+    std::fill(g.begin(), g.end(), 0);
+    for (int it = 0; it < 64; ++it) {
+      bool moved = false;
+      scan_exponents(d, vals, star, s_knot, instr, e, g, nt, true, false, false, st);
+      for (int64_t i = 0; i < n; ++i)
+        if (st.rcnt[i] > 0) {
+          const int m = mean_exp(st.rsum[i], st.rcnt[i]);
+          if (m != 0) {
+            e[i] -= m;
+            moved = true;
+          }
+        }
+      scan_exponents(d, vals, star, s_knot, instr, e, g, nt, false, true, false, st);
+      for (int64_t c = 0; c < n_unk; ++c)
+        if (st.ccnt[c] > 0) {
+          const int m = mean_exp(st.csum[c], st.ccnt[c]);
+          if (m != 0) {
+            g[c] -= m;
+            moved = true;
+          }
+        }
+      if (!moved) break;
+    }
+    // a common row exponent is a column one
+    const int e0 = e[0];
+    bool same = true;
+    for (int64_t i = 1; i < n && same; ++i) same = e[i] == e0;
+    if (same) {
+      std::fill(e.begin(), e.end(), 0);
+      for (int& v : g) v += e0;
+    }
+    scan_exponents(d, vals, star, s_knot, instr, e, g, nt, false, false, true, st);
+    for (int64_t c = 0; c < n_unk; ++c)
+      if (st.cmax[c] != NO_EXP) g[c] -= st.cmax[c];
+    mn = scan_exponents(d, vals, star, s_knot, instr, e, g, nt, false, false, false, st);
+    if (mn < MAT_WIDE_LO) return GSR_E_UNSUPPORTED;
+    out.row_scaled = !same;
+  }
+  for (int v : e)
+    if (v < INT16_MIN || v > INT16_MAX) return GSR_E_UNSUPPORTED;
+  for (int v : g)
+    if (v < INT16_MIN || v > INT16_MAX) return GSR_E_UNSUPPORTED;
+  out.wide = mn < MAT_BAND_LO;
+  if (out.row_scaled) out.row.assign(e.begin(), e.end());
+  out.col.assign(g.begin(), g.end());
+  return GSR_OK;
+}
+
 // Instrumental entries of every tile of ct rows, split by column group (G
 // groups of bpg consecutive columns), each (tile, group) segment ordered into
 // rounds in which every column occurs at most once (round = earlier
@@ -185,7 +400,9 @@ struct InstrRounds {
 };
 
 void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* instr, int ct,
-                        int G, int bpg, bool want_f32, unsigned nt, InstrRounds& out) {
+                        int G, int bpg, bool want_f32, unsigned nt, const Rescale& rs,
+                        InstrRounds& out) {
+  const int64_t instr_base = 5 * d.n_stars + 3 * d.n_knots;
   const int64_t n = d.n_rows;
   const int64_t n_ct = (n + ct - 1) / ct;
   const int64_t n_seg = n_ct * G;
@@ -236,7 +453,10 @@ void build_instr_rounds(const gsr_dims& d, const double* vals, const int32_t* in
         cur_g = g;
       }
       out.key[e] = ((uint32_t)row << INSTR_BIN_BITS) | bin;
-      const double x = vals[(a + row) * NSLOT + 17 + k];
+      double x = vals[(a + row) * NSLOT + 17 + k];
+      const int ex = (rs.row.empty() ? 0 : rs.row[a + row]) +
+                     (rs.col.empty() ? 0 : rs.col[instr_base + bin]);
+      if (ex) x = std::ldexp(x, ex);
       const float h = (float)x;
       out.vff[e] = make_float2(h, (float)(x - (double)h));
       if (want_f32) out.vf32[e] = h;
@@ -294,6 +514,12 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     for (int r : rc)
       if (r != GSR_OK) return r;
   }
+  // ---- exact power-of-two rescaling into the float-pair range ----
+  Rescale rs;
+  {
+    const int r = choose_rescaling(d, vals, star.data(), s_knot.data(), instr, nt, rs);
+    if (r != GSR_OK) return r;
+  }
   // ---- counting sort of rows by start knot (stable) ----
   const int64_t n_buckets = d.n_knots - 3;
   std::vector<int64_t> knot_start(n_buckets + 1, 0);
@@ -330,7 +556,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   }
   if (ct == 0) return GSR_E_UNSUPPORTED;
   for (;;) {
-    build_instr_rounds(d, vals, instr, ct, G, bpg, want_f32, nt, ir);
+    build_instr_rounds(d, vals, instr, ct, G, bpg, want_f32, nt, rs, ir);
     const int64_t lim = ct_per_sm == 2 ? INSTR_SMEM_HALF : INSTR_SMEM_BUDGET;
     if (instr_smem_bytes(ct, ir.max_ent, bpg, false, ct_bufs) <= lim || ct <= REC_ROWS) break;
     ct >>= 1;  // an unusually full segment: retry with shorter tiles
@@ -346,6 +572,8 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   std::memset(sys, 0, sizeof(*sys));
   sys->device = device;
   sys->dims = d;
+  sys->row_scaled = rs.row_scaled;
+  sys->wide = rs.wide;
   cudaDeviceGetAttribute(&sys->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (sys->num_sms <= 0) sys->num_sms = NUM_SMS_B300;
 
@@ -398,7 +626,17 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   A(dalloc(&sys->ient_key, n_ent));
   A(dalloc(&sys->ient_ff, n_ent));
   if (want_f32) A(dalloc(&sys->ient_f32, n_ent));
-  A(dalloc(&sys->err, 1));
+  if (rc == GSR_OK) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&sys->err_host), sizeof(int),
+                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&sys->err), sys->err_host, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      rc = GSR_E_CUDA;
+    } else {
+      *sys->err_host = GSR_OK;
+    }
+  }
   A(dalloc(&sys->colnorm, (size_t)n_unk));
   A(dalloc(&sys->S.red, 65536));
   A(dalloc(&sys->S.count, 64));
@@ -406,6 +644,13 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   A(dalloc(&sys->S.x3, (size_t)n_buckets * 12));
   A(dalloc(&sys->S.y_ff, (size_t)padded_rows(L)));
   A(dalloc(&sys->S.y_knot, (size_t)n));
+  A(dalloc(&sys->S.guard, 4));
+  A(dalloc(&sys->S.iexp, 32));
+  if (!rs.row.empty()) A(dalloc(&sys->row_exp, rs.row.size()));
+  if (!rs.col.empty()) {
+    A(dalloc(&sys->col_exp, rs.col.size()));
+    A(dalloc(&sys->S.zx, (size_t)n_unk));
+  }
   if (rc != GSR_OK) {
     free_system(sys);
     return rc;
@@ -429,9 +674,15 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   C(cudaMemsetAsync(sys->rec_ff, 0, (size_t)n_recs * Rec<false>::BYTES, st));
   if (want_f32) C(cudaMemsetAsync(sys->rec_f32, 0, (size_t)n_recs * Rec<true>::BYTES, st));
   C(cudaMemsetAsync(sys->S.count, 0, 64 * sizeof(unsigned int), st));
-  C(cudaMemsetAsync(sys->err, 0, sizeof(int), st));
   C(cudaMemsetAsync(sys->colnorm, 0, (size_t)n_unk * sizeof(double), st));
   C(cudaMemsetAsync(sys->S.y_ff, 0, (size_t)padded_rows(L) * sizeof(float2), st));
+  C(cudaMemsetAsync(sys->S.guard, 0, 4 * sizeof(double), st));
+  if (sys->row_exp)
+    C(cudaMemcpyAsync(sys->row_exp, rs.row.data(), rs.row.size() * sizeof(int16_t),
+                      cudaMemcpyHostToDevice, st));
+  if (sys->col_exp)
+    C(cudaMemcpyAsync(sys->col_exp, rs.col.data(), rs.col.size() * sizeof(int16_t),
+                      cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->pos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->knot_start, knot_start.data(), (size_t)(n_buckets + 1) * 8,
                     cudaMemcpyHostToDevice, st));
@@ -457,6 +708,8 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.ient_f32 = sys->ient_f32;
   L.ient_key = sys->ient_key;
   L.err = sys->err;
+  L.row_exp = sys->row_exp;
+  L.col_exp = sys->col_exp;
 
   // ---- chunked upload of the values and indices, laid out on the device ----
   if (n > 0) {
@@ -500,7 +753,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     cudaFree(d_star);
     cudaFree(d_sk);
   }
-  k_sqrt<<<sys->num_sms * 4, 256, 0, st>>>(sys->colnorm, n_unk);
+  k_sqrt<<<sys->num_sms * 4, 256, 0, st>>>(sys->colnorm, sys->col_exp, n_unk);
   C(cudaGetLastError());
   C(cudaStreamSynchronize(st));
   if (e != cudaSuccess) return fail(GSR_E_CUDA);
@@ -511,7 +764,7 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
 
 void destroy_system(gsr_system* s) {
   if (!s) return;
-  cudaSetDevice(s->device);
+  DeviceGuard dg(s->device);
   cudaDeviceSynchronize();
   free_system(s);
 }
@@ -528,8 +781,15 @@ int gsr_create(const gsr_dims* dims, const double* vals, const int64_t* astro_of
                gsr_system** out) {
   if (!dims || !out) return GSR_E_ARG;
   *out = nullptr;
-  return gsr::build_system(dims, vals, astro_off, att_off, instr, device,
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    prev = -1;
+  }
+  const int rc = gsr::build_system(dims, vals, astro_off, att_off, instr, device,
                            static_cast<cudaStream_t>(stream), out);
+  if (prev >= 0) cudaSetDevice(prev);  // leave the caller's current device as it was
+  return rc;
 }
 
 void gsr_destroy(gsr_system* sys) { gsr::destroy_system(sys); }
@@ -557,13 +817,10 @@ int gsr_aprod1_values(gsr_system* sys, int which_values, const double* x, double
   if (!sys || (!x && sys->L.n_unk > 0) || (!y && sys->L.n_rows > 0)) return GSR_E_ARG;
   if (which_values != GSR_VALUES_F64 && which_values != GSR_VALUES_F32) return GSR_E_ARG;
   if (which_values == GSR_VALUES_F32 && !sys->rec_f32) return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = gsr::launch_to_ff(x, nullptr, sys->S.x_ff, sys->L.n_unk, st);
-  if (rc != GSR_OK) return rc;
-  rc = gsr::launch_att_x3(sys, sys->S.x_ff, nullptr, st);
-  if (rc != GSR_OK) return rc;
-  return gsr::launch_aprod1_x3(sys, which_values, sys->S.x_ff, y, st);
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
+  return gsr::aprod1_direct(sys, which_values, x, 0, y, static_cast<cudaStream_t>(stream));
 }
 
 int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double* x,
@@ -571,11 +828,10 @@ int gsr_aprod2_values(gsr_system* sys, int which_values, const double* y, double
   if (!sys || (!x && sys->L.n_unk > 0) || (!y && sys->L.n_rows > 0)) return GSR_E_ARG;
   if (which_values != GSR_VALUES_F64 && which_values != GSR_VALUES_F32) return GSR_E_ARG;
   if (which_values == GSR_VALUES_F32 && !sys->rec_f32) return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = gsr::launch_to_ff_knot(sys, y, sys->S.y_ff, sys->S.y_knot, st);
-  if (rc != GSR_OK) return rc;
-  return gsr::launch_aprod2(sys, which_values, sys->S.y_ff, sys->S.y_knot, x, nullptr, st);
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
+  return gsr::aprod2_direct(sys, which_values, y, x, static_cast<cudaStream_t>(stream));
 }
 
 int gsr_aprod1(gsr_system* sys, const double* x, double* y, void* stream) {
@@ -588,7 +844,9 @@ int gsr_aprod2(gsr_system* sys, const double* y, double* x, void* stream) {
 
 int gsr_column_norms(gsr_system* sys, double* c, void* stream) {
   if (!sys || !c) return GSR_E_ARG;
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   return gsr::cuda_status(cudaMemcpyAsync(c, sys->colnorm, (size_t)sys->L.n_unk * sizeof(double),
                                           cudaMemcpyDeviceToDevice,
                                           static_cast<cudaStream_t>(stream)));

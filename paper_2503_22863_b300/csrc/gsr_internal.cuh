@@ -140,6 +140,45 @@ __device__ __forceinline__ ff ff_from_double(double d) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return __dadd_rn((double)a.h, (double)a.l); }
 
+// Exact widening of a float to double with integer instructions only (no FP64
+// pipe), subnormal floats included: a subnormal m * 2^-149 is renormalised so
+// that its leading bit becomes the implicit one of the double.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  if (e == 0u) {
+    if (m == 0u) return __hiloint2double((int)s, 0);
+    const int p = 31 - __clz((int)m);  // leading bit of m, 0..22
+    // value = 2^(p - 149) * (m / 2^p); mantissa bits below the leading one
+    const uint64_t frac = ((uint64_t)m << (52 - p)) & ((1ULL << 52) - 1ULL);
+    const uint32_t ed = (uint32_t)(p - 149 + 1023);
+    return __hiloint2double((int)(s | (ed << 20) | (uint32_t)(frac >> 32)), (int)(uint32_t)frac);
+  }
+  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
+  return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// ---------------------------------------------------------------------------
+// Range of the float-pair arithmetic. A pair carries FP32's exponent range, so
+// the kernels work on an exactly rescaled problem (powers of two only): the
+// stored coefficients are A' = 2^e_i A_ij 2^g_j (row and column exponents
+// chosen at creation), and an input vector reaches the float-pair kernels only
+// when every nonzero entry of its rescaled form lies in [2^VEC_BAND_LO,
+// 2^VEC_BAND_HI). Then every product of a coefficient in [2^-40, 2^40] with a
+// vector entry stays within [2^-100, 2^100]: both words of every pair are
+// normal FP32 numbers and a product keeps its ~48 bits. Outside the band the
+// same call runs FP64 kernels instead (the guard word decides on the device).
+// ---------------------------------------------------------------------------
+constexpr int MAT_BAND_LO = -40, MAT_BAND_HI = 40;  // ilogb range of coefficients kept as is
+constexpr int MAT_WIDE_LO = -100;                   // below this after rescaling: unsupported
+constexpr int VEC_BAND_LO = -60, VEC_BAND_HI = 60;  // ilogb range of vector entries
+
+// True when the nonzero finite v (or zero) fits the vector band.
+__device__ __forceinline__ bool vec_in_band(double v) {
+  const double a = fabs(v);
+  return a == 0.0 || (a >= 0x1p-60 && a < 0x1p60);
+}
+
 __device__ __forceinline__ ff ff_shfl_xor(ff a, int m) {
   return ff{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
 }
@@ -205,11 +244,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Record an error code in the system's error word. The word lives in mapped
+// pinned host memory (the host reads it at the next call without a
+// synchronisation), so a plain volatile store is used: every writer stores the
+// same code, and atomics on host memory are not available everywhere.
+__device__ __forceinline__ void set_error(int* err, int code) {
+  *reinterpret_cast<volatile int*>(err) = code;
+  __threadfence_system();
+}
 constexpr int WAIT_LIMIT = 1 << 22;  // try_wait rounds before giving up (seconds)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   for (int i = 0; i < WAIT_LIMIT; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicExch(err, GSR_E_TIMEOUT);
+  if (err) set_error(err, GSR_E_TIMEOUT);
   return false;
 }
 
@@ -244,7 +291,12 @@ struct Layout {
   const float2* ient_ff;                // coefficient (pair) of each entry; every segment
   const float* ient_f32;                // starts at a multiple of 4 entries (padding
   const uint32_t* ient_key;             // between); key (row in tile << 15) | column
-  int* err;                             // device error word (GSR_E_TIMEOUT)
+  int* err;                             // error word (GSR_E_TIMEOUT), device alias of
+                                        // mapped pinned host memory
+  // exact power-of-two rescaling of the stored coefficients, A' = 2^e A 2^g
+  // (null when every exponent is 0)
+  const int16_t* row_exp;               // [n_rows] e_i
+  const int16_t* col_exp;               // [n_unk]  g_j
 };
 
 struct Scratch {
@@ -255,6 +307,11 @@ struct Scratch {
                         // x[axis*K + s + j] at [s*12 + axis*4 + j] (96 B per start knot)
   float2* y_ff;         // [n_pad] float-pair copy of an aprod 2 input (zero padding)
   float2* y_knot;       // [n_rows] the same in knot order
+  double* guard;        // [4] flags: [0] an aprod input left the float-pair band (the FP64
+                        // kernels run), [1] column scaling check, [2] non-finite
+                        // right-hand side, [3] the same for k right-hand sides
+  int* iexp;            // [32] largest exponent of each right-hand side (LSQR scaling)
+  double* zx;           // [n_unk] aprod 2 accumulator of a column-rescaled system (or null)
 };
 
 }  // namespace gsr

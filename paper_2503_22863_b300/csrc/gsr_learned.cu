@@ -519,7 +519,9 @@ extern "C" int64_t gsr_n_learned_cols(const gsr_system* s) {
 
 extern "C" int gsr_column_features(gsr_system* s, float* feats, void* stream) {
   if (!s || !feats) return GSR_E_ARG;
-  if (cudaSetDevice(s->device) != cudaSuccess) return GSR_E_CUDA;
+  gsr::DeviceGuard dg(s->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(s)) return se;  // an earlier launch failed
   cudaStream_t st = (cudaStream_t)stream;
   const Layout& L = s->L;
   if (!s->instr_count) {
@@ -585,7 +587,9 @@ extern "C" int gsr_mlp_adam(float* theta, const float* grad, float* mom, float* 
 extern "C" int gsr_learned_scaling(gsr_system* s, const float* m, float clamp, double* d,
                                    void* stream) {
   if (!s || !d || !(clamp >= 0.0f)) return GSR_E_ARG;
-  if (cudaSetDevice(s->device) != cudaSuccess) return GSR_E_CUDA;
+  gsr::DeviceGuard dg(s->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(s)) return se;  // an earlier launch failed
   if (s->L.n_unk > 0)
     k_learned_scaling<<<grid_for(s->L.n_unk, 256, s->num_sms * 8), 256, 0,
                         (cudaStream_t)stream>>>(s->L, s->colnorm, m, clamp, d);

@@ -14,6 +14,7 @@
 // replayed in chunks; all kernels return immediately once the stop flag is
 // set, so the host reads the flag only once per chunk.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -27,6 +28,7 @@ enum Scal {
   S_RHO, S_C, S_S, S_THETA, S_PHI, S_T1, S_T2, S_RNORM, S_ARNORM, S_ACOND,
   S_ATOL, S_BTOL, S_CTOL, S_ITN, S_ITNLIM, S_ISTOP, S_DONE,
   S_UNORM2, S_VNORM2, S_COEF_U, S_ERR2, S_XREF2, S_RED3, S_RED3B, S_RED3C,
+  S_BEXP,  // b is solved as 2^-S_BEXP b (largest |b_i| in [1, 2)); x, norms scaled back
   S_COUNT
 };
 
@@ -94,17 +96,93 @@ __device__ bool grid_sum3(double& a, double& b, double& c, double* part, unsigne
   return true;
 }
 
+// The same for four sums (vec_b); returns true in the last block, thread 0
+// then holding the totals.
+__device__ bool grid_sum4(double& a, double& b, double& c, double& d, double* part,
+                          unsigned int* counter) {
+  __shared__ double sh4[32];
+  __shared__ int is_last4;
+  double v[4] = {a, b, c, d};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double x = warp_sum_d(v[q]);
+    __syncthreads();
+    if (lane == 0) sh4[wid] = x;
+    __syncthreads();
+    x = lane < nw ? sh4[lane] : 0.0;
+    v[q] = warp_sum_d(x);  // block total, valid in every warp
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = v[q];
+    __threadfence();
+    is_last4 = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last4) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double x = 0.0;
+    for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) x += __ldcg(part + 4 * i + q);
+    x = warp_sum_d(x);
+    __syncthreads();
+    if (lane == 0) sh4[wid] = x;
+    __syncthreads();
+    x = lane < nw ? sh4[lane] : 0.0;
+    v[q] = warp_sum_d(x);
+  }
+  if (threadIdx.x == 0) {
+    a = v[0];
+    b = v[1];
+    c = v[2];
+    d = v[3];
+    *counter = 0u;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
-// Start: u~ = b (and its knot-order copy), ||b||^2.
+// Largest binary exponent over the nonzero entries of b into *mx (atomicMax,
+// *mx preset very negative); a NaN or Inf entry sets *bad. LSQR is invariant
+// under b -> 2^-s b (x and the residual norms scale by 2^-s), so the solve runs
+// on b with its largest entry in [1, 2): whatever the magnitude of b, the
+// float-pair vectors then neither overflow nor underflow as a whole.
 // ---------------------------------------------------------------------------
-__global__ void k_init_u(Layout L, const double* __restrict__ b, float2* __restrict__ u,
-                         float2* __restrict__ u_knot, double* scal, double* part,
-                         unsigned int* counter) {
+__global__ void k_maxexp(const double* __restrict__ b, int64_t n, int* mx, double* bad) {
+  int m = INT_MIN;
+  bool nonfinite = false;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[r];
+    if (!isfinite(v)) nonfinite = true;
+    else if (v != 0.0) m = max(m, ilogb(v));
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m != INT_MIN) atomicMax(mx, m);
+  if (nonfinite) *bad = 1.0;
+}
+
+// The exponent s of 2^-s b (0 for b = 0).
+__device__ __forceinline__ int b_exponent(const int* mx) {
+  const int m = *mx;
+  return m < -4000 ? 0 : m;
+}
+
+// ---------------------------------------------------------------------------
+// Start: u~ = 2^-s b (and its knot-order copy), ||u~||^2.
+// ---------------------------------------------------------------------------
+__global__ void k_init_u(Layout L, const double* __restrict__ b, const int* bexp,
+                         float2* __restrict__ u, float2* __restrict__ u_knot, double* scal,
+                         double* part, unsigned int* counter) {
   const int32_t* pos = L.pos;
+  const int sb = b_exponent(bexp);
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BEXP] = sb;
   double s2 = 0.0, z0 = 0.0, z1 = 0.0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const double v = b[r];
+    const double v = ldexp(b[r], -sb);
     const ff f = ff_from_double(v);
     u[r] = make_float2(f.h, f.l);
     u_knot[pos[r]] = make_float2(f.h, f.l);
@@ -192,19 +270,24 @@ __global__ void k_vec_a(int64_t n, const float2* __restrict__ d, const double* _
 // vec_b: normalise v, update x and w, write D v as float pairs, ||x||,
 // ||d_k||^2 and the variance; then (last block) the stopping tests.
 // ---------------------------------------------------------------------------
+// With column exponents (cexp) the float-pair D' = 2^-g D v carries them, so
+// x = 2^g D' z is formed in FP64 for ||x|| and the error (its entries may span
+// more than FP32's range).
 __global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restrict__ v,
                         float2* __restrict__ w, float2* __restrict__ xz,
                         float2* __restrict__ v_ff, double* __restrict__ var,
                         const double* __restrict__ x_ref, const double* __restrict__ x_off,
-                        double* scal, double* part, unsigned int* counter, int first,
-                        double* err_hist, double* rnorm_hist) {
+                        const int16_t* __restrict__ cexp, double* scal, double* part,
+                        unsigned int* counter, int first, double* err_hist, double* rnorm_hist) {
   if (scal[S_DONE] != 0.0) return;
+  const int sb = (int)scal[S_BEXP];
+  double x2d = 0.0;
   const double alpha = scal[S_ALPHA];
   const ff ia = ff_from_double(alpha > 0.0 ? 1.0 / alpha : 0.0);
   const ff irho = ff_from_double(first ? 1.0 : 1.0 / scal[S_RHO]);
   const ff t1 = ff_from_double(first ? 0.0 : scal[S_T1]);
   const ff t2 = ff_from_double(first ? 0.0 : scal[S_T2]);
-  ff dk2f = ff_zero(), x2f = ff_zero();
+  ff dk2f = ff_zero(), x2f = ff_zero(), z2f = ff_zero();
   double e2 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < n;
@@ -242,23 +325,30 @@ __global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restr
         if (var) var[j] += ff_to_double(dd);
         const ff xn = ff_norm(ff_add(ff{xf.x, xf.y}, ff_mul(t1, wj)));
         xz[j] = make_float2(xn.h, xn.l);
+        z2f = ff_add(z2f, ff_mul(xn, xn));
         const ff wn = ff_norm(ff_add(vn, ff_mul(t2, wj)));
         w[j] = make_float2(wn.h, wn.l);
         xv = ff_norm(ff_mul(dj, xn));
-        x2f = ff_add(x2f, ff_mul(xv, xv));
+        if (cexp) {
+          const double xd = ldexp(ff_to_double(xv), (int)cexp[j]);
+          x2d = __fma_rn(xd, xd, x2d);
+        } else {
+          x2f = ff_add(x2f, ff_mul(xv, xv));
+        }
       }
       v[j] = make_float2(vn.h, vn.l);
       const ff f = ff_norm(ff_mul(dj, vn));
       v_ff[j] = make_float2(f.h, f.l);
       if (x_ref) {
-        const double xd = ff_to_double(xv);
+        double xd = ff_to_double(xv);
+        xd = ldexp(xd, sb + (cexp ? (int)cexp[j] : 0));
         const double e = (x_off ? xd + x_off[j] : xd) - x_ref[j];
         e2 = __fma_rn(e, e, e2);
       }
     }
   }
-  double dk2 = ff_to_double(dk2f), x2 = ff_to_double(x2f);
-  if (!grid_sum3(dk2, x2, e2, part, counter) || threadIdx.x != 0) return;
+  double dk2 = ff_to_double(dk2f), x2 = ff_to_double(x2f) + x2d, z2 = ff_to_double(z2f);
+  if (!grid_sum4(dk2, x2, e2, z2, part, counter) || threadIdx.x != 0) return;
   if (first) return;
   const double itn = scal[S_ITN] + 1.0;
   scal[S_ITN] = itn;
@@ -279,13 +369,16 @@ __global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restr
     const double xr2 = scal[S_XREF2];
     err_hist[k] = xr2 > 0.0 ? sqrt(e2 / xr2) : sqrt(e2);
   }
-  if (rnorm_hist) rnorm_hist[k] = rnorm;
+  if (rnorm_hist) rnorm_hist[k] = ldexp(rnorm, sb);
   const double atol = scal[S_ATOL], btol = scal[S_BTOL], ctol = scal[S_CTOL];
+  // the tests belong to the preconditioned system the loop solves (Sec. 2,
+  // solver step 2): ||A D|| and the norm of its iterate z; ||x|| is reported
+  const double znorm = sqrt(z2);
   const double test1 = rnorm / bnorm;
   const double test2 = (anorm * rnorm > 0.0) ? arnorm / (anorm * rnorm) : 0.0;
   const double test3 = 1.0 / acond;
-  const double t1n = test1 / (1.0 + anorm * xnorm / bnorm);
-  const double rtol = btol + atol * anorm * xnorm / bnorm;
+  const double t1n = test1 / (1.0 + anorm * znorm / bnorm);
+  const double rtol = btol + atol * anorm * znorm / bnorm;
   int istop = 0;
   if (itn >= scal[S_ITNLIM]) istop = 7;
   if (1.0 + test3 <= 1.0) istop = 6;
@@ -298,6 +391,38 @@ __global__ void k_vec_b(int64_t n, const float2* __restrict__ d, float2* __restr
   if (istop != 0) scal[S_DONE] = 1.0;
 }
 
+// Sec. 2.2, Eq. 4 for the chosen pairs: cov[p] += d_k[j1] d_k[j2] with the
+// direction d_k = w_k / rho_k of this iteration (w still the old one: the
+// kernel runs after vec_a has computed rho and before vec_b updates w).
+__global__ void k_cov(int64_t n_cov, const int64_t* __restrict__ pairs,
+                      const float2* __restrict__ w, const double* scal,
+                      double* __restrict__ cov) {
+  if (scal[S_DONE] != 0.0) return;
+  const double irho = 1.0 / scal[S_RHO];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_cov;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = w[pairs[2 * p]], b = w[pairs[2 * p + 1]];
+    const double d1 = ff_to_double(ff{a.x, a.y}) * irho, d2 = ff_to_double(ff{b.x, b.y}) * irho;
+    cov[p] = __fma_rn(d1, d2, cov[p]);
+  }
+}
+
+// *bad = 1 if any pair has an index outside [0, n).
+__global__ void k_cov_check(int64_t n_cov, const int64_t* __restrict__ pairs, int64_t n,
+                            double* bad) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < 2 * n_cov;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (pairs[p] < 0 || pairs[p] >= n) *bad = 1.0;
+}
+
+// cov[p] *= d[j1] d[j2] (de-precondition).
+__global__ void k_cov_finish(int64_t n_cov, const int64_t* __restrict__ pairs,
+                             const double* __restrict__ d, double* __restrict__ cov) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_cov;
+       p += (int64_t)gridDim.x * blockDim.x)
+    cov[p] *= d[pairs[2 * p]] * d[pairs[2 * p + 1]];
+}
+
 __global__ void k_sumsq(int64_t n, const double* __restrict__ a, double* scal, int slot,
                         double* part, unsigned int* counter) {
   double s2 = 0.0, z0 = 0.0, z1 = 0.0;
@@ -307,9 +432,12 @@ __global__ void k_sumsq(int64_t n, const double* __restrict__ a, double* scal, i
   if (grid_sum3(s2, z0, z1, part, counter) && threadIdx.x == 0) scal[slot] = s2;
 }
 
+// Column scaling D (Sec. 2 solver step 2) in FP64, and the float pairs of
+// D' = 2^-g D that the products use (A D = A' D' with A' = A 2^g). *bad = 2 for
+// a scale that is not positive and finite, 1 for a D' outside the vector band.
 __global__ void k_scale_setup(int64_t n, int mode, const double* __restrict__ colnorm,
-                              const double* __restrict__ user, double* __restrict__ d,
-                              float2* __restrict__ d_ff) {
+                              const double* __restrict__ user, const int16_t* __restrict__ cexp,
+                              double* __restrict__ d, float2* __restrict__ d_ff, double* bad) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double s = 1.0;
@@ -320,19 +448,24 @@ __global__ void k_scale_setup(int64_t n, int mode, const double* __restrict__ co
       s = user[j];
     }
     d[j] = s;
-    const ff f = ff_from_double(s);
+    const double sp = cexp ? ldexp(s, -(int)cexp[j]) : s;
+    if (!(s > 0.0) || !isfinite(s)) *bad = 2.0;
+    else if (!vec_in_band(sp)) *bad = 1.0;
+    const ff f = ff_from_double(sp);
     d_ff[j] = make_float2(f.h, f.l);
   }
 }
 
-// x = D z (de-precondition, Sec. 2 solver step 5); var = D^2 var.
+// x = 2^s D z (de-precondition, Sec. 2 solver step 5, and undo the scaling of
+// b); var = D^2 var.
 __global__ void k_finish(int64_t n, const double* __restrict__ d, const float2* __restrict__ xz,
-                         double* __restrict__ x, double* __restrict__ var) {
+                         const double* scal, double* __restrict__ x, double* __restrict__ var) {
+  const int sb = (int)scal[S_BEXP];
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const double dj = d[j];
     const float2 z = xz[j];
-    x[j] = dj * ff_to_double(ff{z.x, z.y});
+    x[j] = dj * ldexp(ff_to_double(ff{z.x, z.y}), sb);
     if (var) var[j] *= dj * dj;
   }
 }
@@ -381,6 +514,9 @@ struct Ctx {
   const double* x_off;
   double* err_dev;
   double* rn_dev;
+  int64_t n_cov;
+  const int64_t* cov_pairs;
+  double* cov;
 };
 
 constexpr int LAUNCHES_PER_ITERATION = 8;  // x3, aprod1, zero, aprod2 (3), vec_a, vec_b
@@ -397,15 +533,24 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   rc = launch_aprod1_ff(s, c.which_values, s->v_ff, s->u, scal + S_COEF_U, s->u_knot,
                             scal + S_UNORM2, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
+  rc = con_aprod1_lsqr(s, s->v_ff, scal + S_COEF_U, scal + S_UNORM2, scal + S_DONE, c.st);
+  if (rc != GSR_OK) return rc;
   k_zero<<<vb, 256, 0, c.st>>>(L.n_unk, s->z, scal);
   if (ev) cudaEventRecordWithFlags(ev[1], c.st, cudaEventRecordExternal);
   rc = launch_aprod2(s, c.which_values, s->u, s->u_knot, s->z, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
+  rc = con_aprod2_lsqr(s, s->z, scal + S_DONE, c.st);
+  if (rc != GSR_OK) return rc;
   if (ev) cudaEventRecordWithFlags(ev[2], c.st, cudaEventRecordExternal);
   k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->z, s->v, scal, s->S.red,
                                 s->S.count + 1, 0);
+  if (c.n_cov > 0) {
+    const int cb = (int)std::min<int64_t>((c.n_cov + 255) / 256, (int64_t)s->num_sms * 4);
+    k_cov<<<cb, 256, 0, c.st>>>(c.n_cov, c.cov_pairs, s->w, scal, c.cov);
+  }
   k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
-                                c.x_off, scal, s->S.red, s->S.count + 2, 0, c.err_dev, c.rn_dev);
+                                c.x_off, L.col_exp, scal, s->S.red, s->S.count + 2, 0, c.err_dev,
+                                c.rn_dev);
   if (ev) cudaEventRecordWithFlags(ev[3], c.st, cudaEventRecordExternal);
   return cuda_status(cudaGetLastError());
 }
@@ -434,7 +579,27 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   h[S_CTOL] = o->conlim > 0.0 ? 1.0 / o->conlim : 0.0;
   h[S_ITNLIM] = (double)itnlim;
   C(cudaMemcpyAsync(scal, h, sizeof(h), cudaMemcpyHostToDevice, st));
-  C(cudaStreamSynchronize(st));  // h is a stack buffer
+  // exponent of the largest |b_i| (and a check that b is finite); the
+  // covariance pairs' indexes
+  const int64_t n_cov = (o->cov && o->cov_pairs) ? o->n_cov : 0;
+  C(cudaMemsetAsync(s->S.iexp, 0x80, sizeof(int), st));
+  C(cudaMemsetAsync(s->S.guard + 2, 0, 2 * sizeof(double), st));
+  {
+    const int64_t n_eq = L.n_rows + s->n_con;
+    const int eb = (int)std::min<int64_t>(RED_BLOCKS, (n_eq + 255) / 256 + 1);
+    k_maxexp<<<eb, 256, 0, st>>>(b, n_eq, s->S.iexp, s->S.guard + 2);
+  }
+  if (n_cov > 0)
+    k_cov_check<<<(int)std::min<int64_t>((2 * n_cov + 255) / 256, 148 * 4), 256, 0, st>>>(
+        n_cov, o->cov_pairs, L.n_unk, s->S.guard + 3);
+  C(cudaGetLastError());
+  double flags[2] = {0.0, 0.0};
+  C(cudaMemcpyAsync(flags, s->S.guard + 2, sizeof(flags), cudaMemcpyDeviceToHost, st));
+  C(cudaStreamSynchronize(st));  // h and flags are stack buffers
+  if (e != cudaSuccess) return GSR_E_CUDA;
+  if (flags[0] != 0.0) return GSR_E_NONFINITE;
+  if (flags[1] != 0.0) return GSR_E_INDEX;
+  if (n_cov > 0) C(cudaMemsetAsync(o->cov, 0, n_cov * sizeof(double), st));
   // per-iteration histories
   double* err_dev = nullptr;
   double* rn_dev = nullptr;
@@ -446,21 +611,29 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (o->var) k_zero<<<vb, 256, 0, st>>>(L.n_unk, o->var, nullptr);
   k_zero<<<vb, 256, 0, st>>>(L.n_unk, reinterpret_cast<double*>(s->xz), nullptr);
   // start: beta_1 u_1 = b, alpha_1 v_1 = (A D)^T u_1, w_1 = v_1, x_0 = 0
-  k_init_u<<<rb, 256, 0, st>>>(L, b, s->u, s->u_knot, scal, s->S.red, s->S.count + 4);
+  k_init_u<<<rb, 256, 0, st>>>(L, b, s->S.iexp, s->u, s->u_knot, scal, s->S.red,
+                               s->S.count + 4);
+  int rc = con_init_lsqr(s, b + L.n_rows, scal + S_BEXP, scal + S_UNORM2, st);
+  if (rc != GSR_OK) return rc;
   k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->z, nullptr);
-  int rc = launch_aprod2(s, which_values, s->u, s->u_knot, s->z, nullptr, st);
+  rc = launch_aprod2(s, which_values, s->u, s->u_knot, s->z, nullptr, st);
+  if (rc != GSR_OK) return rc;
+  rc = con_aprod2_lsqr(s, s->z, nullptr, st);
   if (rc != GSR_OK) return rc;
   k_vec_a<<<vb, 256, 0, st>>>(L.n_unk, s->dscale_ff, s->z, s->v, scal, s->S.red, s->S.count + 1,
                               1);
   k_vec_b<<<vb, 256, 0, st>>>(L.n_unk, s->dscale_ff, s->v, s->w, s->xz, s->v_ff, o->var,
-                              o->x_ref && err_dev ? o->x_ref : nullptr, x_off, scal, s->S.red,
-                              s->S.count + 2, 1, nullptr, nullptr);
+                              o->x_ref && err_dev ? o->x_ref : nullptr, x_off, L.col_exp, scal,
+                              s->S.red, s->S.count + 2, 1, nullptr, nullptr);
   C(cudaGetLastError());
   if (e != cudaSuccess) return GSR_E_CUDA;
 
-  int64_t n_launches = 7 + (o->var ? 1 : 0) + ((o->x_ref && err_dev) ? 1 : 0);
-  Ctx c{s, st, which_values, o->var, (o->x_ref && err_dev) ? o->x_ref : nullptr, x_off, err_dev,
-        rn_dev};
+  int64_t n_launches = 8 + (o->var ? 1 : 0) + ((o->x_ref && err_dev) ? 1 : 0) +
+                       (s->n_con > 0 ? (s->con_nseg > 0 ? 2 : 1) : 0);
+  Ctx c{s,      st,     which_values, o->var, (o->x_ref && err_dev) ? o->x_ref : nullptr,
+        x_off,  err_dev, rn_dev,      n_cov,  o->cov_pairs,
+        o->cov};
+  if (n_cov > 0) n_launches += 1;  // the check
   // Capture a chunk of iterations once and replay it.
   const int chunk = 4;
   const bool prof = o->profile != 0;
@@ -515,7 +688,8 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
       }
     }
     launched += chunk;
-    n_launches += (int64_t)chunk * LAUNCHES_PER_ITERATION;
+    n_launches += (int64_t)chunk * (LAUNCHES_PER_ITERATION + (n_cov > 0 ? 1 : 0) +
+                                    (s->n_con > 0 ? (s->con_nseg > 0 ? 4 : 2) : 0));
     C(cudaMemcpyAsync(s->host_scal, scal, S_COUNT * 8, cudaMemcpyDeviceToHost, st));
     C(cudaStreamSynchronize(st));
     if (e != cudaSuccess || rc != GSR_OK) break;
@@ -548,7 +722,12 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   }
   const double* hs = s->host_scal;
   const int64_t itn = (int64_t)hs[S_ITN];
-  if (x) k_finish<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->xz, x, o->var);
+  if (x) k_finish<<<vb, 256, 0, st>>>(L.n_unk, s->dscale, s->xz, scal, x, o->var);
+  if (n_cov > 0) {
+    k_cov_finish<<<(int)std::min<int64_t>((n_cov + 255) / 256, 148 * 4), 256, 0, st>>>(
+        n_cov, o->cov_pairs, s->dscale, o->cov);
+    ++n_launches;
+  }
   if (o->err_hist && err_dev && itn > 0)
     C(cudaMemcpyAsync(o->err_hist, err_dev, itn * 8, cudaMemcpyDeviceToHost, st));
   if (o->rnorm_hist && rn_dev && itn > 0)
@@ -557,13 +736,14 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (rn_dev) C(cudaFreeAsync(rn_dev, st));
   C(cudaStreamSynchronize(st));
   if (e != cudaSuccess) return GSR_E_CUDA;
+  const int sb = (int)hs[S_BEXP];
   res->istop = (int32_t)hs[S_ISTOP];
   res->itn = itn;
-  res->rnorm = hs[S_RNORM];
-  res->arnorm = hs[S_ARNORM];
+  res->rnorm = std::ldexp(hs[S_RNORM], sb);
+  res->arnorm = std::ldexp(hs[S_ARNORM], sb);
   res->anorm = std::sqrt(hs[S_ANORM2]);
   res->acond = hs[S_ACOND];
-  res->xnorm = hs[S_XNORM];
+  res->xnorm = std::ldexp(hs[S_XNORM], sb);
   res->n_launches = n_launches + (x ? 1 : 0);
   res->n_timed_itn = timed;
   res->t_aprod1_ms = t_a1;
@@ -588,11 +768,20 @@ __global__ void k_axpy_into(int64_t n, double a, const double* __restrict__ xa,
 //            both products, so its fixed point is the full-precision solution.
 int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
                gsr_lsqr_result* res, cudaStream_t st, int64_t itnlim) {
-  const int64_t n = s->L.n_rows, m = s->L.n_unk;
+  const int64_t n = s->L.n_rows + s->n_con, m = s->L.n_unk;  // equations, unknowns
+  if (s->mx_r_len < n) {  // the residual vector follows the constraint count
+    if (s->mx_r) cudaFree(s->mx_r);
+    s->mx_r = nullptr;
+    s->mx_r_len = 0;
+    if (cudaMalloc((void**)&s->mx_r, (n > 0 ? n : 1) * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return GSR_E_OOM;
+    }
+    s->mx_r_len = n;
+  }
   if (!s->mx_x1) {
     cudaError_t e = cudaMalloc((void**)&s->mx_x1, m * 8);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->mx_d, m * 8);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->mx_r, (n > 0 ? n : 1) * 8);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
@@ -618,15 +807,14 @@ int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (m + 255) / 256 + 1);
   cudaError_t e = cudaMemcpyAsync(s->mx_r, b, n * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return GSR_E_CUDA;
-  rc = launch_to_ff_neg(s->mx_x1, s->S.x_ff, m, st);
-  if (rc != GSR_OK) return rc;
-  rc = launch_att_x3(s, s->S.x_ff, nullptr, st);
-  if (rc != GSR_OK) return rc;
-  rc = launch_aprod1_x3(s, GSR_VALUES_F64, s->S.x_ff, s->mx_r, st);
+  rc = aprod1_direct(s, GSR_VALUES_F64, s->mx_x1, 1, s->mx_r, st);
   if (rc != GSR_OK) return rc;
   // phase 2
   gsr_lsqr_opts o2 = *o;
   o2.var = nullptr;
+  o2.n_cov = 0;
+  o2.cov = nullptr;
+  o2.cov_pairs = nullptr;
   const int64_t n1 = r1.itn;
   o2.err_hist = o->err_hist ? o->err_hist + n1 : nullptr;
   o2.rnorm_hist = o->rnorm_hist ? o->rnorm_hist + n1 : nullptr;
@@ -637,7 +825,7 @@ int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o
   if (cudaStreamSynchronize(st) != cudaSuccess) return GSR_E_CUDA;
   res->phase2_itn = (int32_t)res->itn;
   res->itn += n1;
-  res->n_launches += r1.n_launches + 5;
+  res->n_launches += r1.n_launches + 6;
   res->n_timed_itn += r1.n_timed_itn;
   res->t_aprod1_ms += r1.t_aprod1_ms;
   res->t_aprod2_ms += r1.t_aprod2_ms;
@@ -645,11 +833,22 @@ int lsqr_mixed(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o
   return GSR_OK;
 }
 
+// D and D'; GSR_E_ARG for a user scale that is not positive and finite,
+// GSR_E_UNSUPPORTED for one that D' = 2^-g D takes outside the vector band.
 int setup_scaling(gsr_system* s, const gsr_lsqr_opts* o, cudaStream_t st) {
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (s->L.n_unk + 255) / 256 + 1);
-  k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->dscale,
-                                    s->dscale_ff);
-  return cuda_status(cudaGetLastError());
+  if (cudaMemsetAsync(s->S.guard + 1, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  k_scale_setup<<<vb, 256, 0, st>>>(s->L.n_unk, o->precond, s->colnorm, o->scale, s->L.col_exp,
+                                    s->dscale, s->dscale_ff, s->S.guard + 1);
+  double bad = 0.0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&bad, s->S.guard + 1, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GSR_E_CUDA;
+  if (bad == 2.0) return GSR_E_ARG;
+  if (bad != 0.0) return GSR_E_UNSUPPORTED;
+  return GSR_OK;
 }
 
 }  // namespace gsr
@@ -677,21 +876,31 @@ int gsr_lsqr_solve(gsr_system* sys, const double* b, double* x, const gsr_lsqr_o
   if (opts->precision == GSR_PREC_MIXED && !sys->rec_f32) return GSR_E_ARG;
   if (opts->atol < 0 || opts->btol < 0 || opts->conlim < 0 || opts->itnlim < 0) return GSR_E_ARG;
   if ((opts->err_hist && !opts->x_ref)) return GSR_E_ARG;
+  if (opts->n_cov < 0 || (opts->n_cov > 0 && (!opts->cov_pairs || !opts->cov))) return GSR_E_ARG;
+  // rows rescaled by different powers of two cannot be folded into the column
+  // preconditioner (they would reweight the least-squares problem)
+  if (sys->row_scaled) return GSR_E_UNSUPPORTED;
   std::memset(res, 0, sizeof(*res));
-  if (cudaSetDevice(sys->device) != cudaSuccess) return GSR_E_CUDA;
+  gsr::DeviceGuard dg(sys->device);
+  if (!dg.ok) return GSR_E_CUDA;
+  if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = gsr::ensure_work(sys);
   if (rc != GSR_OK) return rc;
   rc = gsr::setup_scaling(sys, opts, st);
   if (rc != GSR_OK) return rc;
   const int64_t itnlim = opts->itnlim > 0 ? opts->itnlim : 20 * std::max<int64_t>(1, sys->L.n_unk);
-  if (sys->L.n_rows == 0 || sys->L.n_unk == 0) {
+  if (sys->L.n_rows + sys->n_con == 0 || sys->L.n_unk == 0) {
     if (x && sys->L.n_unk > 0) cudaMemsetAsync(x, 0, sys->L.n_unk * 8, st);
     res->istop = 0;
     return gsr::cuda_status(cudaStreamSynchronize(st));
   }
-  if (opts->precision == GSR_PREC_MIXED) return gsr::lsqr_mixed(sys, b, x, opts, res, st, itnlim);
-  return gsr::lsqr_run(sys, b, x, opts, res, st, GSR_VALUES_F64, nullptr, itnlim);
+  rc = opts->precision == GSR_PREC_MIXED
+           ? gsr::lsqr_mixed(sys, b, x, opts, res, st, itnlim)
+           : gsr::lsqr_run(sys, b, x, opts, res, st, GSR_VALUES_F64, nullptr, itnlim);
+  // the solve has synchronised: a failed bounded wait of any of its kernels shows here
+  if (rc == GSR_OK) rc = gsr::sticky_error(sys);
+  return rc;
 }
 
 }  // extern "C"

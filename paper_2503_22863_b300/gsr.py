@@ -43,7 +43,8 @@ class LsqrOpts(ctypes.Structure):
     _fields_ = [("atol", _c_dbl), ("btol", _c_dbl), ("conlim", _c_dbl), ("itnlim", _c_i64),
                 ("precond", _c_i32), ("precision", _c_i32), ("scale", _c_p), ("var", _c_p),
                 ("x_ref", _c_p), ("err_hist", _c_p), ("rnorm_hist", _c_p),
-                ("mixed_switch_itn", _c_i32), ("profile", _c_i32)]
+                ("mixed_switch_itn", _c_i32), ("profile", _c_i32),
+                ("n_cov", _c_i64), ("cov_pairs", _c_p), ("cov", _c_p)]
 
 
 class LsqrResult(ctypes.Structure):
@@ -70,6 +71,10 @@ def _load():
     lib.gsr_n_unknowns.restype = _c_i64
     lib.gsr_n_rows.argtypes = [_c_p]
     lib.gsr_n_rows.restype = _c_i64
+    lib.gsr_n_equations.argtypes = [_c_p]
+    lib.gsr_n_equations.restype = _c_i64
+    lib.gsr_set_constraints.argtypes = [_c_p, _c_i64, _c_p, _c_p, _c_p, _c_p]
+    lib.gsr_set_constraints.restype = ctypes.c_int
     for name in ("gsr_aprod1", "gsr_aprod2"):
         getattr(lib, name).argtypes = [_c_p, _c_p, _c_p, _c_p]
         getattr(lib, name).restype = ctypes.c_int
@@ -154,9 +159,26 @@ class System:
         self._h = h
         self.n_rows = int(lib.gsr_n_rows(h))
         self.n_unk = int(lib.gsr_n_unknowns(h))
+        self.n_eq = self.n_rows
+        if sys.get("con_ptr") is not None:
+            self.set_constraints(sys["con_ptr"], sys["con_col"], sys["con_val"])
         self.n_stars, self.n_knots = int(sys["n_stars"]), int(sys["n_knots"])
         self.n_instr, self.n_glob = int(sys["n_instr"]), int(sys["n_glob"])
         self.storage = storage
+
+    def set_constraints(self, con_ptr, con_col, con_val):
+        """Constraint rows in CSR form (host arrays; gsr_set_constraints). Vectors
+        over the equations then have n_eq = n_rows + n_con entries."""
+        ptr = np.ascontiguousarray(con_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(con_col, dtype=np.int64)
+        val = np.ascontiguousarray(con_val, dtype=np.float64)
+        if ptr.ndim != 1 or ptr.size < 1 or col.shape != val.shape or ptr[-1] != col.size:
+            raise ValueError("constraints must be CSR arrays: ptr[n_con + 1], col[nnz], val[nnz]")
+        with torch.cuda.device(self.device):
+            _check(lib.gsr_set_constraints(self._h, ptr.size - 1, ptr.ctypes.data_as(_c_p),
+                                           col.ctypes.data_as(_c_p), val.ctypes.data_as(_c_p),
+                                           _stream()), "gsr_set_constraints")
+        self.n_eq = int(lib.gsr_n_equations(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -178,7 +200,7 @@ class System:
     def aprod1(self, x, y, values="f64"):
         """Eq. 2: y += A x (in place on the tensor y)."""
         code = lib.gsr_aprod1_values(self._h, VALUES_F32 if values == "f32" else VALUES_F64,
-                                     _dptr(x, self.n_unk, "x"), _dptr(y, self.n_rows, "y"),
+                                     _dptr(x, self.n_unk, "x"), _dptr(y, self.n_eq, "y"),
                                      _stream())
         _check(code, "gsr_aprod1")
         return y
@@ -186,7 +208,7 @@ class System:
     def aprod2(self, y, x, values="f64"):
         """Eq. 3: x += A^T y (in place on the tensor x)."""
         code = lib.gsr_aprod2_values(self._h, VALUES_F32 if values == "f32" else VALUES_F64,
-                                     _dptr(y, self.n_rows, "y"), _dptr(x, self.n_unk, "x"),
+                                     _dptr(y, self.n_eq, "y"), _dptr(x, self.n_unk, "x"),
                                      _stream())
         _check(code, "gsr_aprod2")
         return x
@@ -198,8 +220,9 @@ class System:
 
     def lsqr(self, b, x=None, atol=1e-12, btol=1e-12, conlim=1e12, itnlim=0, precond="colnorm",
              precision="f64", scale=None, want_var=False, x_ref=None, err_hist=False,
-             rnorm_hist=False, mixed_switch_itn=0, profile=False):
-        """Preconditioned LSQR (gsr_lsqr_solve). Returns a dict with x and the result fields."""
+             rnorm_hist=False, mixed_switch_itn=0, profile=False, cov_pairs=None):
+        """Preconditioned LSQR (gsr_lsqr_solve). Returns a dict with x and the result fields;
+        cov_pairs (a CUDA int64 tensor [n, 2]) adds "cov", the covariance estimates."""
         o = LsqrOpts()
         lib.gsr_lsqr_default_opts(ctypes.byref(o))
         o.atol, o.btol, o.conlim, o.itnlim = atol, btol, conlim, int(itnlim)
@@ -215,6 +238,16 @@ class System:
             o.var = var.data_ptr()
         if x_ref is not None:
             o.x_ref = _dptr(x_ref, self.n_unk, "x_ref").value
+        cov = None
+        if cov_pairs is not None:
+            if not isinstance(cov_pairs, torch.Tensor) or cov_pairs.dim() != 2 or \
+                    cov_pairs.shape[1] != 2:
+                raise ValueError("cov_pairs must be a tensor of shape (n, 2)")
+            npair = int(cov_pairs.shape[0])
+            o.cov_pairs = _dptr(cov_pairs, 2 * npair, "cov_pairs", dtype=torch.int64).value
+            cov = torch.zeros(npair, dtype=torch.float64, device=self.device)
+            o.n_cov = npair
+            o.cov = cov.data_ptr() if npair > 0 else None
         lim = int(itnlim) if itnlim else 20 * max(1, self.n_unk)
         eh = rh = None
         if err_hist:
@@ -228,7 +261,7 @@ class System:
         if x is None:
             x = torch.empty(self.n_unk, dtype=torch.float64, device=self.device)
         r = LsqrResult()
-        code = lib.gsr_lsqr_solve(self._h, _dptr(b, self.n_rows, "b"), _dptr(x, self.n_unk, "x"),
+        code = lib.gsr_lsqr_solve(self._h, _dptr(b, self.n_eq, "b"), _dptr(x, self.n_unk, "x"),
                                   ctypes.byref(o), ctypes.byref(r), _stream())
         _check(code, "gsr_lsqr_solve")
         out = dict(x=x, istop=r.istop, itn=r.itn, phase2_itn=r.phase2_itn, rnorm=r.rnorm,
@@ -238,6 +271,8 @@ class System:
                    t_vector_ms=r.t_vector_ms)
         if var is not None:
             out["var"] = var
+        if cov is not None:
+            out["cov"] = cov
         if eh is not None:
             out["err_hist"] = eh[:r.itn]
         if rh is not None:

@@ -11,7 +11,11 @@ LSQR_TOL = 1e-9
 
 
 def abs_system(sys):
-    return dict(sys, vals=np.abs(sys["vals"]))
+    """|A| (constraint rows included) for the accuracy scale |A||x|."""
+    out = dict(sys, vals=np.abs(sys["vals"]))
+    if sys.get("con_val") is not None:
+        out["con_val"] = np.abs(sys["con_val"])
+    return out
 
 
 def aprod1_ref(sys, x, y0):

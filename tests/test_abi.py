@@ -143,3 +143,28 @@ def test_binding_refuses_host_tensors(gsr):
         gsr._dptr2(torch.zeros((3, 2), dtype=torch.float64), 3, 2, "X")
     with pytest.raises(TypeError):
         gsr._dptr(np.zeros(3), 3, "x")
+
+
+def test_create_rescaling_decision_on_host(gsr):
+    """gsr_create's range check runs on the host before the device: a spread that
+    no power-of-two row and column scaling removes is GSR_E_UNSUPPORTED; a row
+    scaled far beyond FP32's range is accepted (rescaled exactly)."""
+    base = _tiny()
+    # rows 0 and 1 share star 0's astrometric columns 0 and 1; the 2 x 2 minor
+    # a00 a11 / (a01 a10) = 1e70 is the same under every diagonal scaling, so
+    # one of a01, a10 stays below 2^-100 of its row and column maxima
+    s = dict(base, vals=base["vals"].copy())
+    s["vals"][0, 0], s["vals"][0, 1] = 1.0, 1e-70
+    s["vals"][1, 0], s["vals"][1, 1] = 1.0, 1.0
+    assert _create(gsr, s) == 8                          # GSR_E_UNSUPPORTED
+    # a diagonal scaling of an N(0,1) matrix is removable, however wide: row 3
+    # times 1e200 and the global column (slot 23 of every row) times 1e-250
+    s = dict(base, vals=base["vals"].copy())
+    s["vals"][3, :] *= 1e200
+    s["vals"][:, 23] *= 1e-250
+    code = _create(gsr, s)
+    assert code != 8 and code in (0, 6), code            # 6: no device on this host
+    # subnormal FP64 coefficients are finite values: accepted
+    s = dict(base, vals=base["vals"] * 1e-310)
+    code = _create(gsr, s)
+    assert code in (0, 6), code

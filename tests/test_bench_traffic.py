@@ -1,7 +1,8 @@
 """Host logic of the benchmark's roofline `traffic` field: DRAM bytes per launch
-come from a committed ncu summary only while that summary was taken on the
-current kernel source; a one-pass capture of the very workload wins over the
-small-workload counters scaled by rows."""
+come from the ncu figures in profiles/traffic.json only while they were taken
+on the current kernel source; a capture of the very workload wins over a
+smaller workload's bytes per row scaled by rows."""
+import json
 import os
 import sys
 
@@ -19,14 +20,18 @@ def _use(tmp_path, monkeypatch, h):
 def _write_profiles(tmp_path, h, medium=True):
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "aprod1_small.md").write_text(
-        "kernel_source_hash: %s\n\ndram_bytes_per_row: 240.5\n" % h)
-    (prof / "aprod2_small.md").write_text(
-        "kernel_source_hash: %s\n\ndram_bytes_per_row: 250.0\n" % h)
+    entries = [
+        {"kernel": "aprod1", "workload": "small", "bytes_per_row": 240.5, "kernel_source_hash": h},
+        {"kernel": "aprod2", "workload": "small", "bytes_per_row": 250.0, "kernel_source_hash": h},
+    ]
     if medium:
-        (prof / "dram_medium.md").write_text(
-            "kernel_source_hash: %s\nn_rows: 1000\n\naprod1_bytes_per_launch: 262000\n"
-            "aprod2_bytes_per_launch: 251000\n" % h)
+        entries += [
+            {"kernel": "aprod1", "workload": "medium", "n_rows": 1000, "bytes_per_launch": 262000,
+             "kernel_source_hash": h},
+            {"kernel": "aprod2", "workload": "medium", "n_rows": 1000, "bytes_per_launch": 251000,
+             "kernel_source_hash": h},
+        ]
+    (prof / "traffic.json").write_text(json.dumps({"entries": entries}))
 
 
 def test_direct_capture_wins_for_its_workload(tmp_path, monkeypatch):

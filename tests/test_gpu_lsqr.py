@@ -69,6 +69,22 @@ def test_lsqr_preconditioners_same_answer(gsr, precond):
     assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
 
 
+def test_lsqr_rank_deficient_minimum_norm(gsr):
+    # stars with 1-4 rows, empty knot and instrumental columns: the result is
+    # the minimum-norm solution of the column-scaled problem, as the oracle's
+    # (itself pinned to D pinv(A D) b on the CPU)
+    sys = synth.rank_deficient_system()
+    b = rhs(sys)
+    ref = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
+    c = np.sqrt(oracle.colnorm2(sys))
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, itnlim=5000)
+        x = to_host(r["x"])
+    assert r["istop"] in (1, 2), r["istop"]
+    assert relerr(x, ref["x"]) <= LSQR_TOL
+    assert not x[c == 0].any()
+
+
 def test_lsqr_planted_solution(gsr):
     sys = synth.make_system(n_stars=2000, n_knots=300, n_instr=100, n_glob=0, obs=20, seed=22,
                             x_star="ones")
@@ -140,3 +156,37 @@ def test_lsqr_medium_normal_equations(gsr):
     anorm_scaled = np.sqrt(np.count_nonzero(c))
     test2 = np.linalg.norm(d * atr) / (anorm_scaled * np.linalg.norm(res))
     assert test2 <= 1e-10, test2
+
+
+def test_lsqr_covariance_pairs(gsr, tiny):
+    """Sec. 2.2, Eq. 4 for chosen pairs: the GPU's estimate against the oracle's
+    on the same solve (the oracle's is pinned to the dense inverse on the CPU).
+    Like the variance, the estimate is a sum over the run, so it is compared at
+    the variance's tolerance, relative to sqrt(var_j1 var_j2); a pair (j, j)
+    reproduces the variance, and a pair with an index outside [0, N_unk) is
+    refused with GSR_E_INDEX."""
+    sys, b, ref = tiny
+    n = sys["n_unk"]
+    K, ni = sys["n_knots"], sys["n_instr"]
+    ab, ib = 5 * sys["n_stars"], 5 * sys["n_stars"] + 3 * K
+    rng = np.random.default_rng(11)
+    pairs = np.concatenate([
+        np.array([[0, 1], [0, 4], [5, 9], [ab, ab + 1], [ab, ab + K], [ib, ib + 3],
+                  [ib + 2, n - 1], [n - 1, 0], [ab + 7, 3]]),
+        rng.integers(0, n, size=(500, 2)),
+        np.stack([np.arange(0, n, 97)] * 2, axis=1),          # diagonal pairs
+    ]).astype(np.int64)
+    o = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14, want_var=True, cov_pairs=pairs)
+    with gsr.System(sys) as S:
+        r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, want_var=True,
+                   cov_pairs=torch.from_numpy(pairs).cuda())
+        cov, var = to_host(r["cov"]), to_host(r["var"])
+        bad = pairs[:3].copy()
+        bad[1, 1] = n
+        with pytest.raises(gsr.GsrError) as e:
+            S.lsqr(to_dev(b), cov_pairs=torch.from_numpy(bad).cuda())
+        assert e.value.code == 2
+    den = np.sqrt(o["var"][pairs[:, 0]] * o["var"][pairs[:, 1]])
+    assert np.max(np.abs(cov - o["cov"]) / den) < 1e-3
+    diag = pairs[:, 0] == pairs[:, 1]
+    np.testing.assert_allclose(cov[diag], var[pairs[diag, 0]], rtol=1e-12)

@@ -1,10 +1,17 @@
-"""The allocation-free aprod 1 entry point (gsr_aprod1_noalloc) against gsr_aprod1.
+"""The allocation-free aprod 1 entry point (gsr_aprod1_noalloc).
 
-Some callers cannot allocate device memory at call time (graph capture, memory
-held by another allocator, latency-critical loops); gsr_aprod1_noalloc stages
-its scratch in a fixed device array of the library instead. This file is
-collected last so that a stop-at-first-failure run has run every other test
-before it; it passes alone in a fresh process as well."""
+Some callers cannot allocate device memory at call time: a process whose GPU
+memory is already held by another framework's caching allocator, or a
+latency-critical loop that cannot take the device-wide synchronisation of
+cudaMalloc/cudaFree. gsr_aprod1_noalloc stages its scratch in a fixed device
+array of the library instead. Each call here is checked against gsr_aprod1 and
+against the FP64 oracle (1e-12 scaled by |A||x|), two calls in a row (they
+share the static array), over the launcher's configurations: instrumental
+unknowns staged in shared memory, the one-buffer configuration for up to
+~20,000 of them, gathered through L2 beyond that, no global column, a partial
+last record, and inputs outside the float-pair range (the FP64 kernel).
+This file is collected last so that a stop-at-first-failure run has run every
+other test before it; it passes alone in a fresh process as well."""
 import ctypes
 
 import numpy as np
@@ -33,8 +40,21 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def test_noalloc_matches_aprod1_two_calls(gsr):
-    sys_ = synth.make_system(n_stars=20000, n_knots=2000, n_instr=700, n_glob=1, obs=30, seed=61)
+SHAPES = [
+    # instrumental unknowns staged in shared memory beside two buffers per pair
+    dict(n_stars=20000, n_knots=2000, n_instr=700, n_glob=1, obs=30, seed=61),
+    # 6,144 < n_instr <= ~20,000: five pairs with one record buffer each
+    dict(n_stars=3000, n_knots=500, n_instr=8000, n_glob=1, obs=30, seed=63),
+    # beyond that: instrumental unknowns gathered through L1/L2
+    dict(n_stars=3000, n_knots=500, n_instr=24576, n_glob=1, obs=30, seed=64),
+    # no global column; 1,001 rows (partial last record)
+    dict(n_stars=143, n_knots=40, n_instr=12, n_glob=0, obs=7, poisson=False, seed=65),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "i%d_g%d" % (s["n_instr"], s["n_glob"]))
+def test_noalloc_matches_aprod1_and_oracle_two_calls(gsr, shape):
+    sys_ = synth.make_system(**shape)
     rng = np.random.default_rng(4)
     with gsr.System(sys_) as S:
         for call in range(2):  # two calls in a row share the static scratch
@@ -46,8 +66,27 @@ def test_noalloc_matches_aprod1_two_calls(gsr):
             assert gsr.lib.gsr_aprod1_noalloc(S._h, _ptr(x), _ptr(y_new), _stream()) == 0
             torch.cuda.synchronize()
             a, b = y_new.cpu().numpy(), y_ref.cpu().numpy()
-            _, scale = aprod1_ref(sys_, x.cpu().numpy(), y0)
+            ref, scale = aprod1_ref(sys_, x.cpu().numpy(), y0)
             assert scaled_err(a, b, scale) <= APROD_TOL, call
+            assert scaled_err(a, ref, scale) <= APROD_TOL, call
+
+
+def test_noalloc_wide_inputs(gsr):
+    """x spanning 1e-30 .. 1e30 (outside the float-pair band: the FP64 kernel),
+    then an in-band x on the same system (the float-pair kernel again)."""
+    sys_ = synth.make_system(n_stars=500, n_knots=80, n_instr=40, n_glob=1, obs=20, seed=66)
+    rng = np.random.default_rng(5)
+    with gsr.System(sys_) as S:
+        for wide in (True, False):
+            xh = rng.standard_normal(S.n_unk)
+            if wide:
+                xh *= 10.0 ** rng.uniform(-30, 30, S.n_unk)
+            x = torch.from_numpy(xh).cuda()
+            y = torch.zeros(S.n_rows, dtype=torch.float64, device="cuda")
+            assert gsr.lib.gsr_aprod1_noalloc(S._h, _ptr(x), _ptr(y), _stream()) == 0
+            torch.cuda.synchronize()
+            ref, scale = aprod1_ref(sys_, xh, np.zeros(S.n_rows))
+            assert scaled_err(y.cpu().numpy(), ref, scale) <= APROD_TOL, wide
 
 
 def test_noalloc_rejects_too_many_unknowns(gsr):
