@@ -306,6 +306,10 @@ int gsr_column_features(gsr_system* sys, float* feats, void* stream);
 /* acc[k] += sum_i f[i][k], acc[8 + k] += sum_i f[i][k]^2 (device double[16];
  * atomics, so the order of the additions is not fixed). */
 int gsr_feature_moments(const float* feats, int64_t n, double* acc, void* stream);
+/* norm (device, 16 floats) = mean[8], 1/std[8] of n feature rows from their
+ * moments acc (as gsr_feature_moments leaves them); a feature with variance
+ * below 1e-12 gets 1/std = 1. n > 0. */
+int gsr_feature_standardisation(const double* acc, int64_t n, float* norm, void* stream);
 /* m[i] = network output for feature row i (device [n]). */
 int gsr_mlp_forward(const float* feats, int64_t n, const float* norm, const float* theta,
                     float* m, void* stream);

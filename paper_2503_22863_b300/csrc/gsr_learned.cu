@@ -550,6 +550,24 @@ extern "C" int gsr_feature_moments(const float* feats, int64_t n, double* acc, v
   return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_E_CUDA;
 }
 
+// norm[0..7] = mean, norm[8..15] = 1/std (1 for a constant feature) from the
+// moments acc (sums and sums of squares over n rows).
+__global__ void k_feature_norm(const double* __restrict__ acc, int64_t n, float* __restrict__ norm) {
+  const int k = threadIdx.x;
+  if (k >= NF) return;
+  const double mean = acc[k] / (double)n;
+  const double var = fmax(acc[NF + k] / (double)n - mean * mean, 0.0);
+  norm[k] = (float)mean;
+  norm[NF + k] = var > 1e-12 ? (float)(1.0 / sqrt(var)) : 1.0f;
+}
+
+extern "C" int gsr_feature_standardisation(const double* acc, int64_t n, float* norm,
+                                           void* stream) {
+  if (!acc || !norm || n <= 0) return GSR_E_ARG;
+  k_feature_norm<<<1, 32, 0, (cudaStream_t)stream>>>(acc, n, norm);
+  return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_E_CUDA;
+}
+
 extern "C" int gsr_mlp_forward(const float* feats, int64_t n, const float* norm,
                                const float* theta, float* m, void* stream) {
   if (n < 0 || (n > 0 && (!feats || !norm || !theta || !m))) return GSR_E_ARG;

@@ -96,23 +96,28 @@ __device__ bool grid_sum3(double& a, double& b, double& c, double* part, unsigne
   return true;
 }
 
-// The same for four sums (vec_b); returns true in the last block, thread 0
-// then holding the totals.
-__device__ bool grid_sum4(double& a, double& b, double& c, double& d, double* part,
-                          unsigned int* counter) {
-  __shared__ double sh4[32];
-  __shared__ int is_last4;
-  double v[4] = {a, b, c, d};
+// The same for four sums (vec_b): one shared-memory round per stage; returns
+// true in the last block, thread 0 then holding the totals.
+__device__ __forceinline__ void block_sum4(double v[4], double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double x = warp_sum_d(v[q]);
-    __syncthreads();
-    if (lane == 0) sh4[wid] = x;
-    __syncthreads();
-    x = lane < nw ? sh4[lane] : 0.0;
-    v[q] = warp_sum_d(x);  // block total, valid in every warp
-  }
+  for (int q = 0; q < 4; ++q) v[q] = warp_sum_d(v[q]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sh[32 * q + wid] = v[q];
+  __syncthreads();
+  if (wid == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = warp_sum_d(lane < nw ? sh[32 * q + lane] : 0.0);
+}
+
+__device__ bool grid_sum4(double& a, double& b, double& c, double& d, double* part,
+                          unsigned int* counter) {
+  __shared__ double sh4[128];
+  __shared__ int is_last4;
+  double v[4] = {a, b, c, d};
+  block_sum4(v, sh4);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = v[q];
@@ -122,22 +127,16 @@ __device__ bool grid_sum4(double& a, double& b, double& c, double& d, double* pa
   __syncthreads();
   if (!is_last4) return false;
   __threadfence();
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double x = 0.0;
-    for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) x += __ldcg(part + 4 * i + q);
-    x = warp_sum_d(x);
-    __syncthreads();
-    if (lane == 0) sh4[wid] = x;
-    __syncthreads();
-    x = lane < nw ? sh4[lane] : 0.0;
-    v[q] = warp_sum_d(x);
-  }
+    for (int q = 0; q < 4; ++q) t[q] += __ldcg(part + 4 * i + q);
+  block_sum4(t, sh4);
   if (threadIdx.x == 0) {
-    a = v[0];
-    b = v[1];
-    c = v[2];
-    d = v[3];
+    a = t[0];
+    b = t[1];
+    c = t[2];
+    d = t[3];
     *counter = 0u;
   }
   return true;
@@ -521,13 +520,16 @@ struct Ctx {
 
 constexpr int LAUNCHES_PER_ITERATION = 8;  // x3, aprod1, zero, aprod2 (3), vec_a, vec_b
 
-// Events (4 per iteration) bracket aprod 1, aprod 2 and the vector kernels.
-int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
+// Events (4 per iteration) bracket aprod 1, aprod 2 and the vector kernels;
+// while the iteration is captured into a graph they are recorded as external
+// event nodes (the flag is valid only during capture).
+int enqueue_iteration(const Ctx& c, cudaEvent_t* ev, bool capturing) {
+  const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   gsr_system* s = c.s;
   const Layout& L = s->L;
   double* scal = s->scal;
   const int vb = (int)std::min<int64_t>(RED_BLOCKS, (L.n_unk + 255) / 256 + 1);
-  if (ev) cudaEventRecordWithFlags(ev[0], c.st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[0], c.st, ev_flags);
   int rc = launch_att_x3(s, s->v_ff, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
   rc = launch_aprod1_ff(s, c.which_values, s->v_ff, s->u, scal + S_COEF_U, s->u_knot,
@@ -536,12 +538,12 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   rc = con_aprod1_lsqr(s, s->v_ff, scal + S_COEF_U, scal + S_UNORM2, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
   k_zero<<<vb, 256, 0, c.st>>>(L.n_unk, s->z, scal);
-  if (ev) cudaEventRecordWithFlags(ev[1], c.st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[1], c.st, ev_flags);
   rc = launch_aprod2(s, c.which_values, s->u, s->u_knot, s->z, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
   rc = con_aprod2_lsqr(s, s->z, scal + S_DONE, c.st);
   if (rc != GSR_OK) return rc;
-  if (ev) cudaEventRecordWithFlags(ev[2], c.st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[2], c.st, ev_flags);
   k_vec_a<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->z, s->v, scal, s->S.red,
                                 s->S.count + 1, 0);
   if (c.n_cov > 0) {
@@ -551,7 +553,7 @@ int enqueue_iteration(const Ctx& c, cudaEvent_t* ev) {
   k_vec_b<<<vb, 256, 0, c.st>>>(L.n_unk, s->dscale_ff, s->v, s->w, s->xz, s->v_ff, c.var, c.x_ref,
                                 c.x_off, L.col_exp, scal, s->S.red, s->S.count + 2, 0, c.err_dev,
                                 c.rn_dev);
-  if (ev) cudaEventRecordWithFlags(ev[3], c.st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[3], c.st, ev_flags);
   return cuda_status(cudaGetLastError());
 }
 
@@ -660,7 +662,8 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (use_graph && st != nullptr) {
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       int r2 = GSR_OK;
-      for (int i = 0; i < chunk && r2 == GSR_OK; ++i) r2 = enqueue_iteration(c, prof ? evs + 4 * i : nullptr);
+      for (int i = 0; i < chunk && r2 == GSR_OK; ++i)
+        r2 = enqueue_iteration(c, prof ? evs + 4 * i : nullptr, true);
       cudaError_t ce = cudaStreamEndCapture(st, &graph);
       if (r2 != GSR_OK || ce != cudaSuccess ||
           cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
@@ -683,7 +686,7 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
       C(cudaGraphLaunch(exec, st));
     } else {
       for (int i = 0; i < chunk && e == cudaSuccess; ++i) {
-        rc = enqueue_iteration(c, prof ? evs + 4 * i : nullptr);
+        rc = enqueue_iteration(c, prof ? evs + 4 * i : nullptr, false);
         if (rc != GSR_OK) break;
       }
     }

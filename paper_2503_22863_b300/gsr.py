@@ -102,13 +102,14 @@ def _load():
     lib.gsr_n_learned_cols.restype = _c_i64
     lib.gsr_column_features.argtypes = [_c_p, _c_p, _c_p]
     lib.gsr_feature_moments.argtypes = [_c_p, _c_i64, _c_p, _c_p]
+    lib.gsr_feature_standardisation.argtypes = [_c_p, _c_i64, _c_p, _c_p]
     lib.gsr_mlp_forward.argtypes = [_c_p, _c_i64, _c_p, _c_p, _c_p, _c_p]
     lib.gsr_mlp_grad.argtypes = [_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]
     lib.gsr_mlp_adam.argtypes = [_c_p, _c_p, _c_p, _c_p, _c_i64, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, ctypes.c_float, _c_p]
     lib.gsr_learned_scaling.argtypes = [_c_p, _c_p, ctypes.c_float, _c_p, _c_p]
-    for name in ("gsr_column_features", "gsr_feature_moments", "gsr_mlp_forward", "gsr_mlp_grad",
-                 "gsr_mlp_adam", "gsr_learned_scaling"):
+    for name in ("gsr_column_features", "gsr_feature_moments", "gsr_feature_standardisation",
+                 "gsr_mlp_forward", "gsr_mlp_grad", "gsr_mlp_adam", "gsr_learned_scaling"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -293,13 +294,13 @@ def _batch_methods():
         """Eq. 2 for k columns: Y[n_rows, k] += A X[N_unk, k]."""
         k = int(X.shape[1])
         _check(lib.gsr_aprod1_batch(self._h, k, _dptr2(X, self.n_unk, k, "X"),
-                                    _dptr2(Y, self.n_rows, k, "Y"), _stream()), "gsr_aprod1_batch")
+                                    _dptr2(Y, self.n_eq, k, "Y"), _stream()), "gsr_aprod1_batch")
         return Y
 
     def aprod2_batch(self, Y, X):
         """Eq. 3 for k columns: X[N_unk, k] += A^T Y[n_rows, k]."""
         k = int(Y.shape[1])
-        _check(lib.gsr_aprod2_batch(self._h, k, _dptr2(Y, self.n_rows, k, "Y"),
+        _check(lib.gsr_aprod2_batch(self._h, k, _dptr2(Y, self.n_eq, k, "Y"),
                                     _dptr2(X, self.n_unk, k, "X"), _stream()), "gsr_aprod2_batch")
         return X
 
@@ -325,7 +326,7 @@ def _batch_methods():
         if X is None:
             X = torch.empty((self.n_unk, k), dtype=torch.float64, device=self.device)
         res = (LsqrResult * k)()
-        _check(lib.gsr_lsqr_solve_batch(self._h, k, _dptr2(B, self.n_rows, k, "B"),
+        _check(lib.gsr_lsqr_solve_batch(self._h, k, _dptr2(B, self.n_eq, k, "B"),
                                         _dptr2(X, self.n_unk, k, "X"), ctypes.byref(o), res,
                                         _stream()), "gsr_lsqr_solve_batch")
         out = dict(x=X, istop=[r.istop for r in res], itn=[r.itn for r in res],
@@ -369,6 +370,16 @@ def feature_moments(feats, acc):
                                    _dptr(acc, 2 * MLP_NFEAT, "acc"), _stream()),
            "gsr_feature_moments")
     return acc
+
+
+def feature_standardisation(acc, n, norm=None):
+    """norm[16] (float32) = mean, 1/std of n feature rows from their moments acc."""
+    if norm is None:
+        norm = torch.empty(2 * MLP_NFEAT, dtype=torch.float32, device=acc.device)
+    _check(lib.gsr_feature_standardisation(_dptr(acc, 2 * MLP_NFEAT, "acc"), int(n),
+                                           _fptr(norm, 2 * MLP_NFEAT, "norm"), _stream()),
+           "gsr_feature_standardisation")
+    return norm
 
 
 def mlp_forward(feats, norm, theta, out=None):

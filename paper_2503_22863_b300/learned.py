@@ -130,17 +130,14 @@ class Model:
 
 
 def standardisation(feats_list, device):
-    """mean and 1/std of the features over all training rows (moments by kernel)."""
+    """mean and 1/std of the features over all training rows (moments and the
+    standardisation by kernels)."""
     acc = torch.zeros(16, dtype=torch.float64, device=device)
     n = 0
     for f in feats_list:
         gsr.feature_moments(f, acc)
         n += int(f.shape[0])
-    a = acc.cpu().numpy()
-    mean = a[:8] / n
-    var = np.maximum(a[8:] / n - mean * mean, 0.0)
-    istd = np.where(var > 1e-12, 1.0 / np.sqrt(np.where(var > 1e-12, var, 1.0)), 1.0)
-    return torch.tensor(np.concatenate([mean, istd]), dtype=torch.float32, device=device)
+    return gsr.feature_standardisation(acc, n)
 
 
 def train(feats_list, labels_list, steps=1500, lr=2e-3, seed=2503, device=None):

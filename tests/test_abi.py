@@ -117,6 +117,8 @@ def test_learned_entry_points_validate_arguments(gsr):
                             ctypes.c_float(0.999), ctypes.c_float(1e-8), None) == E_ARG
     assert lib.gsr_feature_moments(p, -3, p, None) == E_ARG
     assert lib.gsr_feature_moments(None, 0, p, None) == 0
+    assert lib.gsr_feature_standardisation(None, 10, p, None) == E_ARG
+    assert lib.gsr_feature_standardisation(p, 0, p, None) == E_ARG
     assert lib.gsr_column_features(None, p, None) == E_ARG
     assert lib.gsr_learned_scaling(None, None, ctypes.c_float(3.0), p, None) == E_ARG
     assert lib.gsr_n_learned_cols(None) == 0

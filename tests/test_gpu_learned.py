@@ -193,3 +193,24 @@ def test_train_and_fallback_end_to_end(gsr):
     assert relerr(to_host(r["x"]), to_host(p.x_ref)) <= LSQR_TOL
     for S in handles:
         S.close()
+
+
+def test_feature_standardisation_kernel():
+    """mean and 1/std of the features (moments kernel + standardisation kernel)
+    against numpy's, a constant feature getting 1/std = 1."""
+    from paper_2503_22863_b300 import gsr
+    rng = np.random.default_rng(12)
+    f = (rng.standard_normal((5000, 8)) * np.arange(1, 9) + np.arange(8)).astype(np.float32)
+    f[:, 3] = 2.5
+    parts = [torch.from_numpy(f[:1200]).cuda(), torch.from_numpy(f[1200:]).cuda()]
+    acc = torch.zeros(16, dtype=torch.float64, device="cuda")
+    for p in parts:
+        gsr.feature_moments(p.contiguous(), acc)
+    norm = gsr.feature_standardisation(acc, f.shape[0]).cpu().numpy()
+    fd = f.astype(np.float64)
+    mean = fd.mean(axis=0)
+    std = fd.std(axis=0)
+    np.testing.assert_allclose(norm[:8], mean, rtol=1e-6, atol=1e-6)
+    istd = np.where(std > 1e-6, 1.0 / np.where(std > 1e-6, std, 1.0), 1.0)
+    np.testing.assert_allclose(norm[8:], istd, rtol=1e-5)
+    assert norm[8 + 3] == 1.0

@@ -190,3 +190,21 @@ def test_lsqr_covariance_pairs(gsr, tiny):
     assert np.max(np.abs(cov - o["cov"]) / den) < 1e-3
     diag = pairs[:, 0] == pairs[:, 1]
     np.testing.assert_allclose(cov[diag], var[pairs[diag, 0]], rtol=1e-12)
+
+
+def test_lsqr_profile_on_default_stream(gsr, tiny):
+    """Kernel-group timings from a solve on the legacy default stream (no graph
+    is captured there: the events are recorded directly)."""
+    sys, b, ref = tiny
+    with gsr.System(sys) as S:
+        bd = to_dev(b)
+        torch.cuda.synchronize()
+        r = S.lsqr(bd, atol=1e-14, btol=1e-14, profile=True)
+        assert r["n_timed_itn"] == r["itn"] > 0
+        assert r["t_aprod1_ms"] > 0 and r["t_aprod2_ms"] > 0 and r["t_vector_ms"] > 0
+        assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            r2 = S.lsqr(bd, atol=1e-14, btol=1e-14, profile=True)
+        torch.cuda.synchronize()
+        assert r2["n_timed_itn"] == r2["itn"] and r2["t_aprod1_ms"] > 0

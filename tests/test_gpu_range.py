@@ -186,16 +186,18 @@ def test_lsqr_wide_mixed_and_variance(gsr):
     sys, b = lsqr_case(52, 1e-30, 1e-5)
     ref = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
     assert ref["itn"] > 10
-    # the variance (a sum over the run) over the same 60 iterations on both sides,
-    # so the two sums have the same terms; it spans ~1e40 .. 1e110 here
-    ref_v = oracle.lsqr(sys, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=60, want_var=True)
+    # the variance (a sum over the run) over the same 15 iterations on both sides,
+    # before convergence (past it the added terms are rounding noise and the two
+    # runs' sums part), so the two sums have the same terms; it spans ~1e40 ..
+    # 1e110 here
+    ref_v = oracle.lsqr(sys, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=15, want_var=True)
     with gsr.System(sys, storage="f32+f64") as S:
         r = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, precision="mixed", itnlim=5000)
         assert r["phase2_itn"] > 0 and r["itn"] - r["phase2_itn"] > 10
         assert relerr(to_host(r["x"]), ref["x"]) <= LSQR_TOL
-        r = S.lsqr(to_dev(b), atol=0.0, btol=0.0, conlim=0.0, itnlim=60, want_var=True)
+        r = S.lsqr(to_dev(b), atol=0.0, btol=0.0, conlim=0.0, itnlim=15, want_var=True)
         var = to_host(r["var"])
-    assert r["itn"] == 60
+    assert r["itn"] == 15
     assert np.max(np.abs(var - ref_v["var"]) / ref_v["var"]) < 1e-6
 
 
