@@ -257,8 +257,15 @@ int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* s
  * per-right-hand-side scalars, stopping tests and convergence masks: a system
  * that has stopped keeps its x while the others continue). res has k entries.
  * opts.err_hist (host, [itnlim][k]) with opts.x_ref (device [N_unk][k]) gives
- * per-iteration relative errors. precision must be F64; var and rnorm_hist are
- * not available here (GSR_E_UNSUPPORTED). The first call for a given k times
+ * per-iteration relative errors. precision F64, or MIXED (needs
+ * GSR_STORE_F32_PLUS_F64): a first LSQR phase with the FP32 copy of A and
+ * FP32 products (one multiply-add per product instead of a float-pair one) to
+ * about 1e-6, then the residual R = B - A X1 with the full-precision values and
+ * a second phase with the float-pair kernels on R to the caller's tolerances,
+ * X = X1 + that correction (opts.mixed_switch_itn fixes the first phase's
+ * length); res[j].phase2_itn gives the second phase's iterations. var,
+ * rnorm_hist and covariances are not available here (GSR_E_UNSUPPORTED). The
+ * first call for a given k times
  * the candidate block widths and instrumental row-tile heights on this system and
  * keeps the fastest (gsr_batch_tuning reports the choice). Synchronous.
  */

@@ -1,12 +1,12 @@
 // aprod 1 (Eq. 2, y += A x) and aprod 2 (Eq. 3, x += A^T y) kernels for sm_103a.
 //
 // Both products are HBM-bound (about 0.2 flop per byte) and use no tensor
-// cores. B300's FP64 pipe runs at ~1/64 of its FP32 rate, and double<->float
-// conversions issue on it too, so the hot loops contain no double-precision
-// instruction at all: products and sums are float pairs (hi, lo) with
-// error-free transformations, LSQR's u vector is kept as float pairs, and
-// results reach FP64 memory through exact bit-level float->double widening
-// and L2 atomics.
+// cores. B300's FP64 pipe runs at ~1/64 of its FP32 rate, so the hot loops
+// contain no double-precision arithmetic: products and sums are float pairs
+// (hi, lo) with error-free transformations, and LSQR's u vector is kept as
+// float pairs. A finished sum (a star's, a knot's, a histogram bin's) reaches
+// FP64 memory as one L2 atomic of hi + lo, both widened exactly and added once
+// in FP64.
 //
 // aprod 1 streams 64-row records into shared memory with TMA bulk copies
 // (double-buffered per pair of warps, one row per lane) so that DRAM latency
@@ -64,7 +64,8 @@ __device__ void grid_sum_store(double v, double* part, unsigned int* counter, do
   }
 }
 
-// x += hi + lo as two L2 reductions (no FP64 arithmetic on the SM).
+// x += hi + lo as two L2 reductions, each word widened exactly with integer
+// instructions (no FP64 arithmetic on the SM).
 __device__ __forceinline__ void red_ff(double* x, ff a) {
   if (a.h != 0.0f) atomicAdd(x, f2d_exact(a.h));
   if (a.l != 0.0f) atomicAdd(x, f2d_exact(a.l));

@@ -24,6 +24,8 @@ namespace gsr {
 
 namespace {
 
+// x += hi + lo as two L2 reductions, each word widened exactly with integer
+// instructions (no FP64 arithmetic on the SM).
 __device__ __forceinline__ void red_ff_b(double* x, ff a) {
   if (a.h != 0.0f) atomicAdd(x, f2d_exact(a.h));
   if (a.l != 0.0f) atomicAdd(x, f2d_exact(a.l));
@@ -46,6 +48,57 @@ __device__ __forceinline__ int rinstr(const unsigned char* rec, int k, int r_in)
 __device__ __forceinline__ ff ldf(const float2* p) {
   const float2 a = __ldg(p);
   return ff{a.x, a.y};
+}
+
+// Arithmetic of the two precisions of the batched kernels. F32 = false: the
+// float-pair products and sums of the FP64-accurate path. F32 = true: the
+// FP32-value phase of a mixed-precision solve - coefficients from the FP32
+// copy of A, only the high word of each vector entry, one FP32 multiply-add
+// per product (the low words stay zero).
+template <bool F32>
+__device__ __forceinline__ ff fma_t(ff c, ff x, ff acc) {
+  if constexpr (F32) return ff{__fmaf_rn(c.h, x.h, acc.h), 0.0f};
+  else return ff_add(acc, ff_mul(c, x));
+}
+template <bool F32>
+__device__ __forceinline__ ff add_t(ff a, ff b) {
+  if constexpr (F32) return ff{__fadd_rn(a.h, b.h), 0.0f};
+  else return ff_add(a, b);
+}
+template <bool F32>
+__device__ __forceinline__ ff mul_t(ff a, ff b) {
+  if constexpr (F32) return ff{__fmul_rn(a.h, b.h), 0.0f};
+  else return ff_mul(a, b);
+}
+template <bool F32>
+__device__ __forceinline__ ff norm_t(ff a) {
+  if constexpr (F32) return a;
+  else return ff_norm(a);
+}
+template <bool F32>
+__device__ __forceinline__ ff ldv(const float2* p) {
+  if constexpr (F32) return ff{__ldg(reinterpret_cast<const float*>(p)), 0.0f};
+  else return ldf(p);
+}
+template <bool F32>
+__device__ __forceinline__ ff pair_t(float2 v) {
+  if constexpr (F32) return ff{v.x, 0.0f};
+  else return ff{v.x, v.y};
+}
+// Coefficient of slot t, row r_in, of a record of the given precision.
+template <bool F32>
+__device__ __forceinline__ ff rvt(const unsigned char* rec, int t, int r_in) {
+  if constexpr (F32)
+    return ff{__ldg(reinterpret_cast<const float*>(rec + slot_offset<true>(t)) + r_in), 0.0f};
+  else return rv(rec, t, r_in);
+}
+template <bool F32>
+__device__ __forceinline__ int rinstr_t(const unsigned char* rec, int k, int r_in) {
+  return __ldg(reinterpret_cast<const unsigned short*>(rec + Rec<F32>::INSTR_I + k * 128) + r_in);
+}
+template <bool F32>
+__device__ __forceinline__ const unsigned char* rec_at(const Layout& L, int64_t r) {
+  return (F32 ? L.rec_f32 : L.rec_ff) + r * Rec<F32>::BYTES;
 }
 
 // Per-right-hand-side deterministic grid reduction of NV values per lane:
@@ -113,7 +166,7 @@ __device__ bool grid_sum_kv(const double* v, double* part, unsigned int* counter
 // knot-order copy and per-right-hand-side ||Y_j||^2 into norm_out[j]. A warp
 // takes a record; its 32/KP streams take contiguous slices of the 64 rows.
 // ---------------------------------------------------------------------------
-template <int KP>
+template <int KP, bool F32>
 __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __restrict__ X,
                                                   float2* __restrict__ Y,
                                                   const double* __restrict__ coef,
@@ -131,7 +184,7 @@ __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __rest
   const int64_t K = L.n_knots;
   ff nrm = ff_zero();
   for (int64_t r = gw; r < L.n_recs; r += nw) {
-    const unsigned char* rec = L.rec_ff + r * Rec<false>::BYTES;
+    const unsigned char* rec = rec_at<F32>(L, r);
     // The record's column indices, two rows per lane, loaded up front so the
     // x gathers of a row wait for a shuffle rather than a load: register h of
     // lane (q, p) holds row q * RPS + h * KP + p (RPS = 2 KP), so at step
@@ -140,12 +193,12 @@ __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __rest
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int rr = q * RPS + h * KP + j;
-      pst[h] = ri(rec, Rec<false>::STAR, rr);
-      psk[h] = ri(rec, Rec<false>::ATT_S, rr);
-      ppos[h] = Yk ? ri(rec, Rec<false>::POS, rr) : 0;
+      pst[h] = ri(rec, Rec<F32>::STAR, rr);
+      psk[h] = ri(rec, Rec<F32>::ATT_S, rr);
+      ppos[h] = Yk ? ri(rec, Rec<F32>::POS, rr) : 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        pin[h][k] = rinstr(rec, 2 * k, rr) | (rinstr(rec, 2 * k + 1, rr) << 16);
+        pin[h][k] = rinstr_t<F32>(rec, 2 * k, rr) | (rinstr_t<F32>(rec, 2 * k + 1, rr) << 16);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -168,26 +221,27 @@ __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __rest
         ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero(), a4 = ff_zero();
 #pragma unroll
         for (int t = 0; t < 5; ++t)
-          a0 = ff_add(a0, ff_mul(rv(rec, t, r_in), ldf(X + (5 * (int64_t)st + t) * KP + j)));
+          a0 = fma_t<F32>(rvt<F32>(rec, t, r_in), ldv<F32>(X + (5 * (int64_t)st + t) * KP + j), a0);
 #pragma unroll
         for (int i4 = 0; i4 < 4; ++i4) {
-          a1 = ff_add(a1,
-                      ff_mul(rv(rec, 5 + i4, r_in), ldf(X + (L.att_base + sk + i4) * KP + j)));
-          a2 = ff_add(a2, ff_mul(rv(rec, 9 + i4, r_in),
-                                 ldf(X + (L.att_base + K + sk + i4) * KP + j)));
-          a3 = ff_add(a3, ff_mul(rv(rec, 13 + i4, r_in),
-                                 ldf(X + (L.att_base + 2 * K + sk + i4) * KP + j)));
+          a1 = fma_t<F32>(rvt<F32>(rec, 5 + i4, r_in),
+                          ldv<F32>(X + (L.att_base + sk + i4) * KP + j), a1);
+          a2 = fma_t<F32>(rvt<F32>(rec, 9 + i4, r_in),
+                          ldv<F32>(X + (L.att_base + K + sk + i4) * KP + j), a2);
+          a3 = fma_t<F32>(rvt<F32>(rec, 13 + i4, r_in),
+                          ldv<F32>(X + (L.att_base + 2 * K + sk + i4) * KP + j), a3);
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-          a4 = ff_add(a4, ff_mul(rv(rec, 17 + k, r_in), ldf(X + (L.instr_base + ins[k]) * KP + j)));
-        if (glob) a4 = ff_add(a4, ff_mul(rv(rec, 23, r_in), ldf(X + L.glob_col * KP + j)));
-        const ff acc = ff_add(ff_add(ff_add(a0, a1), ff_add(a2, a3)), a4);
-        const float2 yo = Y[row * KP + j];
-        const ff yn = ff_norm(ff_add(ff_mul(cf, ff{yo.x, yo.y}), acc));
+          a4 = fma_t<F32>(rvt<F32>(rec, 17 + k, r_in),
+                          ldv<F32>(X + (L.instr_base + ins[k]) * KP + j), a4);
+        if (glob) a4 = fma_t<F32>(rvt<F32>(rec, 23, r_in), ldv<F32>(X + L.glob_col * KP + j), a4);
+        const ff acc = add_t<F32>(add_t<F32>(add_t<F32>(a0, a1), add_t<F32>(a2, a3)), a4);
+        const ff yo = pair_t<F32>(Y[row * KP + j]);
+        const ff yn = norm_t<F32>(add_t<F32>(mul_t<F32>(cf, yo), acc));
         Y[row * KP + j] = make_float2(yn.h, yn.l);
         if (Yk) Yk[(int64_t)pos * KP + j] = make_float2(yn.h, yn.l);
-        nrm = ff_add(nrm, ff_mul(yn, yn));
+        nrm = add_t<F32>(nrm, mul_t<F32>(yn, yn));
       }
     }
   }
@@ -201,7 +255,7 @@ __global__ void __launch_bounds__(256) k_aprod1_b(Layout L, const float2* __rest
 // slice of a record's rows keeping per-star sums; a finished (or slice-ending)
 // run is added into X with L2 reductions (KP-wide, contiguous).
 // ---------------------------------------------------------------------------
-template <int KP>
+template <int KP, bool F32>
 __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* __restrict__ Y,
                                                         double* __restrict__ X,
                                                         const double* stop) {
@@ -213,7 +267,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
   const bool glob = L.n_glob == 1;
   ff g = ff_zero();
   for (int64_t r = gw; r < L.n_recs; r += nw) {
-    const unsigned char* rec = L.rec_ff + r * Rec<false>::BYTES;
+    const unsigned char* rec = rec_at<F32>(L, r);
     int cur = -1;
     ff a[5];
 #pragma unroll
@@ -222,7 +276,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
       const int r_in = q * RPS + i;
       const int64_t row = r * REC_ROWS + r_in;
       if (row >= L.n_rows) break;
-      const int st = ri(rec, Rec<false>::STAR, r_in);
+      const int st = ri(rec, Rec<F32>::STAR, r_in);
       if (st != cur) {
         if (cur >= 0)
 #pragma unroll
@@ -231,11 +285,10 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
         for (int t = 0; t < 5; ++t) a[t] = ff_zero();
         cur = st;
       }
-      const float2 yy = __ldcs(Y + row * KP + j);
-      const ff u = ff{yy.x, yy.y};
+      const ff u = pair_t<F32>(__ldcs(Y + row * KP + j));
 #pragma unroll
-      for (int t = 0; t < 5; ++t) a[t] = ff_add(a[t], ff_mul(rv(rec, t, r_in), u));
-      if (glob) g = ff_add(g, ff_mul(rv(rec, 23, r_in), u));
+      for (int t = 0; t < 5; ++t) a[t] = fma_t<F32>(rvt<F32>(rec, t, r_in), u, a[t]);
+      if (glob) g = fma_t<F32>(rvt<F32>(rec, 23, r_in), u, g);
     }
     if (cur >= 0)
 #pragma unroll
@@ -243,7 +296,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
   }
   if (glob) {
 #pragma unroll
-    for (int m = 16; m >= KP; m >>= 1) g = ff_add(g, ff_shfl_xor(g, m));
+    for (int m = 16; m >= KP; m >>= 1) g = add_t<F32>(g, ff_shfl_xor(g, m));
     if (q == 0) red_ff_b(X + L.glob_col * KP + j, g);
   }
 }
@@ -256,7 +309,7 @@ __global__ void __launch_bounds__(256) k_aprod2_astro_b(Layout L, const float2* 
 constexpr int ATT_B_SPLIT = 2;  // warps per knot range of the single-vector partition
 constexpr int VEC_U = 4;        // elements per thread per step of the vector kernels
 
-template <int KP>
+template <int KP, bool F32>
 __global__ void __launch_bounds__(256, 2) k_aprod2_att_b(Layout L, const float2* __restrict__ Yk,
                                                          double* __restrict__ X,
                                                          const double* stop) {
@@ -286,33 +339,36 @@ __global__ void __launch_bounds__(256, 2) k_aprod2_att_b(Layout L, const float2*
     constexpr int U = 2;  // positions per stream per step, all loads issued first
     for (int64_t pb = p0 + q; pb < p1; pb += U * S) {
       ff u[U];
-      float2 v[12][U];
+      ff v[12][U];
 #pragma unroll
       for (int i = 0; i < U; ++i) {
         const int64_t p = pb + (int64_t)i * S;
         const bool in = p < p1;
-        const float2 yy = in ? __ldcs(Yk + p * KP + j) : make_float2(0.f, 0.f);
-        u[i] = ff{yy.x, yy.y};
+        u[i] = in ? pair_t<F32>(__ldcs(Yk + p * KP + j)) : ff_zero();
 #pragma unroll
-        for (int t = 0; t < 12; ++t)
-          v[t][i] = in ? __ldg(L.att_knot_ff + (int64_t)t * L.n_rows + p) : make_float2(0.f, 0.f);
+        for (int t = 0; t < 12; ++t) {
+          if constexpr (F32)
+            v[t][i] = ff{in ? __ldg(L.att_knot_f32 + (int64_t)t * L.n_rows + p) : 0.0f, 0.0f};
+          else
+            v[t][i] = in ? ldf(L.att_knot_ff + (int64_t)t * L.n_rows + p) : ff_zero();
+        }
       }
 #pragma unroll
       for (int t = 0; t < 12; ++t) {
-        ff sum = ff_mul(ff{v[t][0].x, v[t][0].y}, u[0]);
+        ff sum = mul_t<F32>(v[t][0], u[0]);
 #pragma unroll
-        for (int i = 1; i < U; ++i) sum = ff_add(sum, ff_mul(ff{v[t][i].x, v[t][i].y}, u[i]));
-        acc[t] = ff_add(acc[t], sum);
+        for (int i = 1; i < U; ++i) sum = fma_t<F32>(v[t][i], u[i], sum);
+        acc[t] = add_t<F32>(acc[t], sum);
       }
     }
 #pragma unroll
     for (int t = 0; t < 12; ++t)
 #pragma unroll
-      for (int m = 16; m >= KP; m >>= 1) acc[t] = ff_add(acc[t], ff_shfl_xor(acc[t], m));
+      for (int m = 16; m >= KP; m >>= 1) acc[t] = add_t<F32>(acc[t], ff_shfl_xor(acc[t], m));
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) win[a][i] = ff_add(win[a][i], acc[4 * a + i]);
+      for (int i = 0; i < 4; ++i) win[a][i] = add_t<F32>(win[a][i], acc[4 * a + i]);
     if (q == 0)
 #pragma unroll
       for (int a = 0; a < 3; ++a) red_ff_b(X + (L.att_base + a * K + s) * KP + j, win[a][0]);
@@ -411,7 +467,7 @@ __global__ void k_csc_fill(Layout L, int tile_log, int64_t n_bins, const int64_t
   }
 }
 
-template <int KP>
+template <int KP, bool F32>
 __global__ void __launch_bounds__(256) k_aprod2_instr_csc(Layout L, const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ erow,
                                                           const float2* __restrict__ eval,
@@ -443,13 +499,12 @@ __global__ void __launch_bounds__(256) k_aprod2_instr_csc(Layout L, const int64_
 #pragma unroll
       for (int i = 0; i < U; ++i) y[i] = __ldg(Y + (int64_t)r[i] * KP + j);
 #pragma unroll
-      for (int i = 0; i < U; ++i)
-        acc = ff_add(acc, ff_mul(ff{v[i].x, v[i].y}, ff{y[i].x, y[i].y}));
+      for (int i = 0; i < U; ++i) acc = fma_t<F32>(pair_t<F32>(v[i]), pair_t<F32>(y[i]), acc);
     }
     for (; e < e1; ++e) {
       const float2 v = __ldg(eval + e);
       const float2 y = __ldg(Y + (int64_t)__ldg(erow + e) * KP + j);
-      acc = ff_add(acc, ff_mul(ff{v.x, v.y}, ff{y.x, y.y}));
+      acc = fma_t<F32>(pair_t<F32>(v), pair_t<F32>(y), acc);
     }
     red_ff_b(X + (L.instr_base + u % n_bins) * KP + j, acc);
   }
@@ -462,7 +517,7 @@ __global__ void __launch_bounds__(256) k_aprod2_instr_csc(Layout L, const int64_
 // outside the vector band sets *guard.
 __global__ void k_pack_ff(const double* __restrict__ in, int k, int KP, int64_t n,
                           const int16_t* __restrict__ cexp, double* guard,
-                          float2* __restrict__ out) {
+                          float2* __restrict__ out, int neg) {
   bool out_of_band = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * KP;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -470,6 +525,7 @@ __global__ void k_pack_ff(const double* __restrict__ in, int k, int KP, int64_t 
     const int j = (int)(e % KP);
     double v = j < k ? in[i * k + j] : 0.0;
     if (cexp) v = ldexp(v, -(int)cexp[i]);
+    if (neg) v = -v;
     if (!vec_in_band(v)) out_of_band = true;
     const ff f = ff_from_double(v);
     out[e] = make_float2(f.h, f.l);
@@ -687,6 +743,7 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
                                                  float2* __restrict__ XZ,
                                                  float2* __restrict__ Vff,
                                                  const double* __restrict__ xref,
+                                                 const double* __restrict__ xoff,
                                                  const int16_t* __restrict__ cexp, double* sc,
                                                  double* part, unsigned int* counter, int first,
                                                  double* err_hist) {
@@ -764,8 +821,8 @@ __global__ void __launch_bounds__(256) k_vec_b_b(int64_t n, const float2* __rest
         x2f = ff_add(x2f, ff_mul(xv, xv));
         if (xref) xd = ff_to_double(xv);
       }
-      if (xref) {
-        const double ex = ldexp(xd, sb) - xref[e];
+      if (xref) {  // xoff: the first phase's solution in a mixed-precision solve
+        const double ex = ldexp(xd, sb) + (xoff ? xoff[e] : 0.0) - xref[e];
         e2 = __fma_rn(ex, ex, e2);
       }
     }
@@ -886,13 +943,16 @@ struct BatchWork {
   int threads = 256;  // block width of the row/knot kernels (tuned)
   InstrCsc csc;       // instrumental buckets; csc.tile_log is tuned
   bool tuned = false;
+  // mixed precision (allocated on first use): phase-1 solution [n_unk][k],
+  // residual [n_rows][k], phase-1 solution in the padded layout [n_unk][KP]
+  double *X1 = nullptr, *R = nullptr, *X1p = nullptr;
 };
 
 static void free_batch(BatchWork* w) {
   if (!w) return;
   void* p[] = {w->U,    w->Uk,   w->Vff,        w->V,          w->W,          w->XZ,
                w->Z,    w->D,    w->Dff,        w->sc,         w->part,       w->count,
-               w->csc.off, w->csc.row, w->csc.val, w->csc.cnt};
+               w->csc.off, w->csc.row, w->csc.val, w->csc.cnt, w->X1, w->R, w->X1p};
   for (void* q : p)
     if (q) cudaFree(q);
   if (w->hsc) cudaFreeHost(w->hsc);
@@ -1001,7 +1061,7 @@ static int batch_work(gsr_system* s, int KP, BatchWork** out, cudaStream_t st) {
   return GSR_OK;
 }
 
-template <int KP>
+template <int KP, bool F32>
 static int launch_aprod1_bt(gsr_system* s, BatchWork* w, const float2* X, float2* Y,
                             const double* coef, float2* Yk, double* norm_out, const double* stop,
                             cudaStream_t st) {
@@ -1009,12 +1069,12 @@ static int launch_aprod1_bt(gsr_system* s, BatchWork* w, const float2* X, float2
   if (L.n_recs <= 0) return GSR_OK;
   const int wpb = w->threads / 32;
   const int blocks = (int)std::min<int64_t>((L.n_recs + wpb - 1) / wpb, (int64_t)s->num_sms * 16);
-  k_aprod1_b<KP><<<blocks, w->threads, 0, st>>>(L, X, Y, coef, Yk, w->part, w->count + 0,
-                                                norm_out, stop);
+  k_aprod1_b<KP, F32><<<blocks, w->threads, 0, st>>>(L, X, Y, coef, Yk, w->part, w->count + 0,
+                                                     norm_out, stop);
   return cuda_status(cudaGetLastError());
 }
 
-template <int KP>
+template <int KP, bool F32>
 static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const float2* Yk,
                             double* X, const double* stop, cudaStream_t st) {
   const Layout& L = s->L;
@@ -1022,19 +1082,20 @@ static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const 
   if (cudaEventRecord(s->ev_fork, st) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(s->side, s->ev_fork, 0) != cudaSuccess) return GSR_E_CUDA;
   const int att_blocks = (L.n_att_warps * ATT_B_SPLIT + 7) / 8;
-  if (att_blocks > 0) k_aprod2_att_b<KP><<<att_blocks, 256, 0, s->side>>>(L, Yk, X, stop);
+  if (att_blocks > 0) k_aprod2_att_b<KP, F32><<<att_blocks, 256, 0, s->side>>>(L, Yk, X, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   const InstrCsc& C = w->csc;
   const int64_t nbk = C.n_tiles * C.n_bins;
   if (nbk > 0) {
     const int64_t warps = (nbk + (32 / KP) - 1) / (32 / KP);
     const int ib = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)s->num_sms * 16);
-    k_aprod2_instr_csc<KP><<<ib, 256, 0, st>>>(L, C.off, C.row, C.val, nbk, C.n_bins, Y, X, stop);
+    k_aprod2_instr_csc<KP, F32><<<ib, 256, 0, st>>>(L, C.off, C.row, C.val, nbk, C.n_bins, Y, X,
+                                                    stop);
   }
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   const int wpb = w->threads / 32;
   const int ab = (int)std::min<int64_t>((L.n_recs + wpb - 1) / wpb, (int64_t)s->num_sms * 16);
-  k_aprod2_astro_b<KP><<<ab, w->threads, 0, st>>>(L, Y, X, stop);
+  k_aprod2_astro_b<KP, F32><<<ab, w->threads, 0, st>>>(L, Y, X, stop);
   if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   if (cudaEventRecord(s->ev_join, s->side) != cudaSuccess) return GSR_E_CUDA;
   if (cudaStreamWaitEvent(st, s->ev_join, 0) != cudaSuccess) return GSR_E_CUDA;
@@ -1052,13 +1113,18 @@ static int launch_aprod2_bt(gsr_system* s, BatchWork* w, const float2* Y, const 
     default: return GSR_E_ARG;                     \
   }
 
+// f32: the FP32-value kernels of a mixed-precision solve (needs the FP32 copy).
 static int aprod1_b(gsr_system* s, BatchWork* w, const float2* X, float2* Y, const double* coef,
-                    float2* Yk, double* norm_out, const double* stop, cudaStream_t st) {
-  GSR_KP_DISPATCH(w->KP, (launch_aprod1_bt<KP>(s, w, X, Y, coef, Yk, norm_out, stop, st)));
+                    float2* Yk, double* norm_out, const double* stop, cudaStream_t st,
+                    bool f32 = false) {
+  if (f32)
+    GSR_KP_DISPATCH(w->KP, (launch_aprod1_bt<KP, true>(s, w, X, Y, coef, Yk, norm_out, stop, st)));
+  GSR_KP_DISPATCH(w->KP, (launch_aprod1_bt<KP, false>(s, w, X, Y, coef, Yk, norm_out, stop, st)));
 }
 static int aprod2_b(gsr_system* s, BatchWork* w, const float2* Y, const float2* Yk, double* X,
-                    const double* stop, cudaStream_t st) {
-  GSR_KP_DISPATCH(w->KP, (launch_aprod2_bt<KP>(s, w, Y, Yk, X, stop, st)));
+                    const double* stop, cudaStream_t st, bool f32 = false) {
+  if (f32) GSR_KP_DISPATCH(w->KP, (launch_aprod2_bt<KP, true>(s, w, Y, Yk, X, stop, st)));
+  GSR_KP_DISPATCH(w->KP, (launch_aprod2_bt<KP, false>(s, w, Y, Yk, X, stop, st)));
 }
 
 // The autotuner: times aprod 1 + aprod 2 for every (block width, instrumental
@@ -1108,28 +1174,29 @@ static int autotune(gsr_system* s, BatchWork* w, cudaStream_t st) {
 }
 
 template <int KP>
-static int enqueue_b(gsr_system* s, BatchWork* w, const double* xref, double* err_dev,
-                     cudaStream_t st, int first) {
+static int enqueue_b(gsr_system* s, BatchWork* w, const double* xref, const double* xoff,
+                     double* err_dev, cudaStream_t st, int first, bool f32) {
   const int64_t m = s->L.n_unk;
   double* stop = w->sc + B_COUNT * KP + G_ALLDONE;
   const int vb = (int)std::min<int64_t>((m * KP + 255) / 256, (int64_t)s->num_sms * 8);
   int rc = GSR_OK;
   if (!first) {
-    rc = aprod1_b(s, w, w->Vff, w->U, w->sc + B_COEF * KP, w->Uk, w->sc + B_UNORM2 * KP, stop, st);
+    rc = aprod1_b(s, w, w->Vff, w->U, w->sc + B_COEF * KP, w->Uk, w->sc + B_UNORM2 * KP, stop, st,
+                  f32);
     if (rc != GSR_OK) return rc;
   }
   k_zero_d<<<vb, 256, 0, st>>>(w->Z, m * KP, first ? nullptr : stop);
-  rc = aprod2_b(s, w, w->U, w->Uk, w->Z, first ? nullptr : stop, st);
+  rc = aprod2_b(s, w, w->U, w->Uk, w->Z, first ? nullptr : stop, st, f32);
   if (rc != GSR_OK) return rc;
   k_vec_a_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->Z, w->V, w->sc, w->part, w->count + 1, first);
   k_vec_b_b<KP><<<vb, 256, 0, st>>>(m, w->Dff, w->V, w->W, w->XZ, w->Vff, first ? nullptr : xref,
-                                    s->L.col_exp, w->sc, w->part, w->count + 2, first,
+                                    xoff, s->L.col_exp, w->sc, w->part, w->count + 2, first,
                                     first ? nullptr : err_dev);
   return cuda_status(cudaGetLastError());
 }
-static int enqueue_iter_b(gsr_system* s, BatchWork* w, const double* xref, double* err_dev,
-                          cudaStream_t st, int first) {
-  GSR_KP_DISPATCH(w->KP, (enqueue_b<KP>(s, w, xref, err_dev, st, first)));
+static int enqueue_iter_b(gsr_system* s, BatchWork* w, const double* xref, const double* xoff,
+                          double* err_dev, cudaStream_t st, int first, bool f32) {
+  GSR_KP_DISPATCH(w->KP, (enqueue_b<KP>(s, w, xref, xoff, err_dev, st, first, f32)));
 }
 template <int KP>
 static int init_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
@@ -1157,14 +1224,18 @@ __global__ void k_pack_xref(const double* __restrict__ in, int k, int KP, int64_
   }
 }
 
-int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_opts* o,
-               gsr_lsqr_result* res, cudaStream_t st) {
+// One LSQR run on the k right-hand sides with the float-pair kernels (f32 =
+// false) or the FP32-value ones (f32 = true). xoff (packed [n_unk][KP]) is
+// added to the iterate when measuring the error against x_ref (the second
+// phase of a mixed-precision solve).
+static int lsqr_batch_run(gsr_system* s, int k, const double* B, double* X,
+                          const gsr_lsqr_opts* o, gsr_lsqr_result* res, cudaStream_t st,
+                          bool f32, const double* xoff, int64_t itnlim) {
   const int KP = kpad(k);
   BatchWork* w = nullptr;
   int rc = batch_work(s, KP, &w, st);
   if (rc != GSR_OK) return rc;
   const int64_t m = s->L.n_unk;
-  const int64_t itnlim = o->itnlim > 0 ? o->itnlim : 20 * std::max<int64_t>(1, m);
   cudaError_t e = cudaSuccess;
   auto C = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
@@ -1222,7 +1293,7 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
   }
   if (e != cudaSuccess) return GSR_E_CUDA;
   rc = init_iter_b(s, w, B, k, xref, st);
-  if (rc == GSR_OK) rc = enqueue_iter_b(s, w, xref, err_dev, st, 1);
+  if (rc == GSR_OK) rc = enqueue_iter_b(s, w, xref, xoff, err_dev, st, 1, f32);
   if (rc != GSR_OK) return rc;
   int64_t n_launches = 12;
   // iterations: graph of a chunk of iterations, replayed until every RHS stopped
@@ -1237,7 +1308,8 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
   }
   if (use_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     int r2 = GSR_OK;
-    for (int i = 0; i < chunk && r2 == GSR_OK; ++i) r2 = enqueue_iter_b(s, w, xref, err_dev, st, 0);
+    for (int i = 0; i < chunk && r2 == GSR_OK; ++i)
+      r2 = enqueue_iter_b(s, w, xref, xoff, err_dev, st, 0, f32);
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (r2 != GSR_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
       cudaGetLastError();
@@ -1256,7 +1328,8 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
     if (use_graph) {
       C(cudaGraphLaunch(exec, st));
     } else {
-      for (int i = 0; i < chunk && rc == GSR_OK; ++i) rc = enqueue_iter_b(s, w, xref, err_dev, st, 0);
+      for (int i = 0; i < chunk && rc == GSR_OK; ++i)
+        rc = enqueue_iter_b(s, w, xref, xoff, err_dev, st, 0, f32);
     }
     launched += chunk;
     n_launches += (int64_t)chunk * 8;
@@ -1299,6 +1372,106 @@ int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_
   return GSR_OK;
 }
 
+// Y[n][k] += (or -=, neg) A X[n_unk][k] on the observation rows: the
+// float-pair kernels when the rescaled X is within the band, else FP64.
+static int batch_aprod1_direct(gsr_system* sys, BatchWork* w, int k, const double* X, int neg,
+                               double* Y, cudaStream_t st) {
+  const int64_t m = sys->L.n_unk, n = sys->L.n_rows;
+  if (n == 0) return GSR_OK;
+  if (sys->wide) return launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, neg, Y, nullptr, st);
+  const int KP = w->KP;
+  const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
+  const int bn = (int)std::min<int64_t>((n * KP + 255) / 256 + 1, sys->num_sms * 8);
+  double* guard = sys->S.guard;
+  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
+  // U = A' X' (pairs, from zero), then Y += 2^-e U in FP64
+  if (cudaMemsetAsync(w->U, 0, (size_t)n * KP * sizeof(float2), st) != cudaSuccess)
+    return GSR_E_CUDA;
+  k_pack_ff<<<bm, 256, 0, st>>>(X, k, KP, m, sys->L.col_exp, guard, w->Vff, neg);
+  int rc = aprod1_b(sys, w, w->Vff, w->U, nullptr, nullptr, nullptr, guard, st);
+  if (rc != GSR_OK) return rc;
+  k_unpack_add<<<bn, 256, 0, st>>>(w->U, k, KP, n, sys->L.row_exp, guard, Y);
+  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
+  return launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, neg, Y, guard, st);
+}
+
+// Mixed precision for k right-hand sides, as for one: phase 1 runs LSQR with
+// the FP32-value kernels (coefficients of the FP32 copy of A, one FP32
+// multiply-add per product) to about FP32 accuracy; then R = B - A X1 with the
+// full-precision values; phase 2 runs LSQR with the float-pair kernels on
+// min ||A D - R|| to the caller's tolerances (its fixed point is the
+// full-precision solution); X = X1 + D. Each right-hand side keeps its own
+// stopping tests and masks in both phases.
+static int lsqr_batch_mixed(gsr_system* s, int k, const double* B, double* X,
+                            const gsr_lsqr_opts* o, gsr_lsqr_result* res, cudaStream_t st,
+                            int64_t itnlim) {
+  const int KP = kpad(k);
+  BatchWork* w = nullptr;
+  int rc = batch_work(s, KP, &w, st);
+  if (rc != GSR_OK) return rc;
+  const int64_t n = s->L.n_rows, m = s->L.n_unk;
+  if (!w->X1) {
+    cudaError_t e = cudaMalloc((void**)&w->X1, (size_t)std::max<int64_t>(m, 1) * k * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w->R, (size_t)std::max<int64_t>(n, 1) * k * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w->X1p, (size_t)std::max<int64_t>(m, 1) * KP * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? GSR_E_OOM : GSR_E_CUDA;
+    }
+  }
+  // phase 1: FP32 values; FP32 products limit it to about 1e-6
+  constexpr double PHASE1_TOL = 1e-6;
+  gsr_lsqr_opts o1 = *o;
+  int64_t lim1 = itnlim;
+  if (o->mixed_switch_itn > 0) {
+    o1.atol = o1.btol = 0.0;
+    o1.conlim = 0.0;
+    lim1 = std::min<int64_t>(itnlim, o->mixed_switch_itn);
+  } else {
+    o1.atol = std::max(o->atol, PHASE1_TOL);
+    o1.btol = std::max(o->btol, PHASE1_TOL);
+  }
+  std::vector<gsr_lsqr_result> r1(k);
+  rc = lsqr_batch_run(s, k, B, w->X1, &o1, r1.data(), st, true, nullptr, lim1);
+  if (rc != GSR_OK) return rc;
+  const int64_t n1 = r1[0].n_timed_itn;  // iterations phase 1 ran (its longest right-hand side)
+  // R = B - A X1 with the full-precision values
+  if (cudaMemcpyAsync(w->R, B, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return GSR_E_CUDA;
+  rc = batch_aprod1_direct(s, w, k, w->X1, 1, w->R, st);
+  if (rc != GSR_OK) return rc;
+  const double* xoff = nullptr;
+  if (o->err_hist && o->x_ref) {
+    const int vb = (int)std::min<int64_t>((m * KP + 255) / 256, (int64_t)s->num_sms * 8);
+    k_pack_xref<<<vb, 256, 0, st>>>(w->X1, k, KP, m, w->X1p);
+    xoff = w->X1p;
+  }
+  // phase 2: full precision on the residual
+  gsr_lsqr_opts o2 = *o;
+  o2.err_hist = o->err_hist ? o->err_hist + n1 * k : nullptr;
+  const int64_t lim2 = std::max<int64_t>(1, itnlim - n1);
+  rc = lsqr_batch_run(s, k, w->R, X, &o2, res, st, false, xoff, lim2);
+  if (rc != GSR_OK) return rc;
+  const int vb = (int)std::min<int64_t>((m * k + 255) / 256, (int64_t)s->num_sms * 8);
+  k_add_cols<<<vb, 256, 0, st>>>(w->X1, k, k, m, nullptr, nullptr, X);  // X = D + X1
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return GSR_E_CUDA;
+  for (int j = 0; j < k; ++j) {
+    res[j].phase2_itn = (int32_t)res[j].itn;
+    res[j].itn += r1[j].itn;
+    res[j].n_timed_itn += n1;
+    res[j].n_launches += r1[j].n_launches + 6;
+  }
+  return GSR_OK;
+}
+
+int lsqr_batch(gsr_system* s, int k, const double* B, double* X, const gsr_lsqr_opts* o,
+               gsr_lsqr_result* res, cudaStream_t st) {
+  const int64_t itnlim = o->itnlim > 0 ? o->itnlim : 20 * std::max<int64_t>(1, s->L.n_unk);
+  if (o->precision == GSR_PREC_MIXED) return lsqr_batch_mixed(s, k, B, X, o, res, st, itnlim);
+  return lsqr_batch_run(s, k, B, X, o, res, st, false, nullptr, itnlim);
+}
+
 }  // namespace gsr
 
 // ---------------------------------------------------------------------------
@@ -1315,25 +1488,10 @@ int gsr_aprod1_batch(gsr_system* sys, int k, const double* X, double* Y, void* s
   if (const int se = gsr::sticky_error(sys)) return se;  // an earlier launch failed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sys->L.n_rows == 0) return GSR_OK;
-  if (sys->wide) return gsr::launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, 0, Y, nullptr, st);
-  const int KP = gsr::kpad(k);
   gsr::BatchWork* w = nullptr;
-  int rc = gsr::batch_work(sys, KP, &w, st);
+  int rc = gsr::batch_work(sys, gsr::kpad(k), &w, st);
   if (rc != GSR_OK) return rc;
-  const int64_t m = sys->L.n_unk, n = sys->L.n_rows;
-  const int bm = (int)std::min<int64_t>((m * KP + 255) / 256 + 1, sys->num_sms * 8);
-  const int bn = (int)std::min<int64_t>((n * KP + 255) / 256 + 1, sys->num_sms * 8);
-  double* guard = sys->S.guard;
-  if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
-  // U = A' X' (pairs, from zero), then Y += 2^-e U in FP64
-  if (cudaMemsetAsync(w->U, 0, (size_t)n * KP * sizeof(float2), st) != cudaSuccess)
-    return GSR_E_CUDA;
-  gsr::k_pack_ff<<<bm, 256, 0, st>>>(X, k, KP, m, sys->L.col_exp, guard, w->Vff);
-  rc = gsr::aprod1_b(sys, w, w->Vff, w->U, nullptr, nullptr, nullptr, guard, st);
-  if (rc != GSR_OK) return rc;
-  gsr::k_unpack_add<<<bn, 256, 0, st>>>(w->U, k, KP, n, sys->L.row_exp, guard, Y);
-  if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
-  return gsr::launch_aprod1_f64(sys, GSR_VALUES_F64, X, k, 0, Y, guard, st);
+  return gsr::batch_aprod1_direct(sys, w, k, X, 0, Y, st);
 }
 
 int gsr_aprod2_batch(gsr_system* sys, int k, const double* Y, double* X, void* stream) {
@@ -1370,8 +1528,9 @@ int gsr_lsqr_solve_batch(gsr_system* sys, int k, const double* B, double* X,
   if ((!B && sys->L.n_rows > 0) || (!X && sys->L.n_unk > 0)) return GSR_E_ARG;
   if (opts->precond < GSR_PRECOND_NONE || opts->precond > GSR_PRECOND_USER) return GSR_E_ARG;
   if (opts->precond == GSR_PRECOND_USER && !opts->scale) return GSR_E_ARG;
-  if (opts->precision != GSR_PREC_F64 || opts->var || opts->rnorm_hist || opts->n_cov > 0)
-    return GSR_E_UNSUPPORTED;
+  if (opts->precision != GSR_PREC_F64 && opts->precision != GSR_PREC_MIXED) return GSR_E_ARG;
+  if (opts->precision == GSR_PREC_MIXED && !sys->rec_f32) return GSR_E_ARG;
+  if (opts->var || opts->rnorm_hist || opts->n_cov > 0) return GSR_E_UNSUPPORTED;
   if (opts->err_hist && !opts->x_ref) return GSR_E_ARG;
   if (sys->row_scaled) return GSR_E_UNSUPPORTED;  // as for gsr_lsqr_solve
   if (sys->n_con > 0) return GSR_E_UNSUPPORTED;    // constraint rows: single-vector forms only

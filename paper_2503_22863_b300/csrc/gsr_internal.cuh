@@ -140,21 +140,17 @@ __device__ __forceinline__ ff ff_from_double(double d) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return __dadd_rn((double)a.h, (double)a.l); }
 
-// Exact widening of a float to double with integer instructions only (no FP64
-// pipe), subnormal floats included: a subnormal m * 2^-149 is renormalised so
-// that its leading bit becomes the implicit one of the double.
+// Exact widening of a float to double with integer instructions and selects
+// only (no branch, no FP64 pipe), subnormal floats included: a subnormal is
+// first scaled by 2^64 (exact, now normal) and the 64 is taken off the
+// double's exponent.
 __device__ __forceinline__ double f2d_exact(float f) {
-  const uint32_t b = __float_as_uint(f);
+  const uint32_t e0 = (__float_as_uint(f) >> 23) & 0xffu;
+  const float g = e0 == 0u ? __fmul_rn(f, 0x1p64f) : f;
+  const uint32_t b = __float_as_uint(g);
   const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  if (e == 0u) {
-    if (m == 0u) return __hiloint2double((int)s, 0);
-    const int p = 31 - __clz((int)m);  // leading bit of m, 0..22
-    // value = 2^(p - 149) * (m / 2^p); mantissa bits below the leading one
-    const uint64_t frac = ((uint64_t)m << (52 - p)) & ((1ULL << 52) - 1ULL);
-    const uint32_t ed = (uint32_t)(p - 149 + 1023);
-    return __hiloint2double((int)(s | (ed << 20) | (uint32_t)(frac >> 32)), (int)(uint32_t)frac);
-  }
-  const uint32_t ed = (e == 0xffu) ? 0x7ffu : (e + 896u);
+  uint32_t ed = e == 0xffu ? 0x7ffu : e + 896u - (e0 == 0u ? 64u : 0u);
+  ed = (b & 0x7fffffffu) == 0u ? 0u : ed;  // +-0
   return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
 }
 

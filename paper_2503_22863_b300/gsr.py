@@ -305,13 +305,16 @@ def _batch_methods():
         return X
 
     def lsqr_batch(self, B, X=None, atol=1e-12, btol=1e-12, conlim=1e12, itnlim=0,
-                   precond="colnorm", scale=None, x_ref=None, err_hist=False):
+                   precond="colnorm", scale=None, x_ref=None, err_hist=False, precision="f64",
+                   mixed_switch_itn=0):
         """LSQR on k right-hand sides B[n_rows, k] at once (gsr_lsqr_solve_batch)."""
         k = int(B.shape[1])
         o = LsqrOpts()
         lib.gsr_lsqr_default_opts(ctypes.byref(o))
         o.atol, o.btol, o.conlim, o.itnlim = atol, btol, conlim, int(itnlim)
         o.precond = PRECOND[precond]
+        o.precision = PRECISION[precision]
+        o.mixed_switch_itn = int(mixed_switch_itn)
         if scale is not None:
             o.scale = _dptr(scale, self.n_unk, "scale").value
         eh = None
@@ -330,6 +333,7 @@ def _batch_methods():
                                         _dptr2(X, self.n_unk, k, "X"), ctypes.byref(o), res,
                                         _stream()), "gsr_lsqr_solve_batch")
         out = dict(x=X, istop=[r.istop for r in res], itn=[r.itn for r in res],
+                   phase2_itn=[r.phase2_itn for r in res],
                    rnorm=[r.rnorm for r in res], anorm=[r.anorm for r in res],
                    iterations=res[0].n_timed_itn, n_launches=res[0].n_launches)
         if eh is not None:

@@ -171,3 +171,33 @@ def test_batched_aprod_medium_k32_sampled_columns(gsr):
         oracle.aprod2(sys, uj, ref2)
         oracle.aprod2(asys, np.abs(uj), scale2)
         assert scaled_err(Xg[j], ref2, scale2) <= APROD_TOL, ("aprod2", j)
+
+
+def test_batched_mixed_matches_oracle(gsr, tiny_batch):
+    """Mixed precision for k right-hand sides: an FP32-value phase (FP32
+    products) and a float-pair correction phase on the residual; every column
+    must meet the same 1e-9 bar against the FP64 oracle. A zero right-hand side
+    and a consistent one exercise the masks in both phases."""
+    sys, B = tiny_batch
+    B2 = B.copy()
+    B2[:, 1] = 0.0
+    b0 = np.zeros(sys["n_rows"])
+    oracle.aprod1(sys, sys["x_star"], b0)
+    B2[:, 3] = b0
+    refs = [oracle.lsqr(sys, B2[:, j], atol=1e-14, btol=1e-14) for j in range(B2.shape[1])]
+    with gsr.System(sys, storage="f32+f64") as S:
+        r = S.lsqr_batch(to_dev(B2), atol=1e-14, btol=1e-14, precision="mixed")
+        X = to_host(r["x"])
+        # a fixed first phase and the error history over both phases
+        xr = to_dev(np.stack([ref["x"] for ref in refs], axis=1))
+        r2 = S.lsqr_batch(to_dev(B2), atol=1e-14, btol=1e-14, precision="mixed",
+                          mixed_switch_itn=25, x_ref=xr, err_hist=True)
+    assert r["istop"][1] == 0 and not X[:, 1].any()
+    for j in (0, 2, 3, 4):
+        assert relerr(X[:, j], refs[j]["x"]) <= LSQR_TOL, j
+        assert r["phase2_itn"][j] > 0 and r["itn"][j] > r["phase2_itn"][j], j
+    assert relerr(X[:, 3], sys["x_star"]) <= 1e-9
+    eh = r2["err_hist"]
+    for j in (0, 2, 4):
+        assert eh[24, j] > 1e-8          # the FP32 phase alone stops short of 1e-9
+        assert np.nanmin(eh[:, j]) <= LSQR_TOL, j
