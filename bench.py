@@ -627,7 +627,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="medium", choices=["tiny", "small", "medium", "large"])
+    ap.add_argument("--workload", default="medium", choices=["tiny", "small", "medium", "large", "large_small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision / batched variants")

@@ -39,6 +39,10 @@ CONFIGS = {
     # still well above the 126 MB L2)
     "small": dict(n_stars=100_000, obs=30, poisson=True, n_knots=20_000, n_instr=2_000,
                   n_glob=1, seed=2510),
+    # profiling case: the large shape (200,000 knots, 20,000 instrumental columns)
+    # at 300,000 stars (~12M rows, ~2.6 GB of records)
+    "large_small": dict(n_stars=300_000, obs=40, poisson=True, n_knots=200_000,
+                        n_instr=20_000, n_glob=1, seed=2511),
 }
 NOISE_SIGMA = 1e-3
 
