@@ -96,7 +96,8 @@ __global__ void k_to_ff(const double* __restrict__ x, const double* __restrict__
 // y (double) -> 2^-e_i y_i as pairs in row order and in knot order; an entry
 // outside the vector band sets *guard.
 __global__ void k_to_ff_knot(Layout L, const double* __restrict__ y, float2* __restrict__ y_ff,
-                             float2* __restrict__ y_knot, double* guard) {
+                             float2* __restrict__ y_knot, const int32_t* __restrict__ kp,
+                             double* guard) {
   bool out_of_band = false;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_rows;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -106,7 +107,7 @@ __global__ void k_to_ff_knot(Layout L, const double* __restrict__ y, float2* __r
     const ff f = ff_from_double(v);
     const float2 w = make_float2(f.h, f.l);
     y_ff[r] = w;
-    y_knot[L.pos[r]] = w;
+    y_knot[kp[r]] = w;
   }
   if (guard && out_of_band) *guard = 1.0;
 }
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(NP * 64, 1)
   const ff coef_ff = ff_from_double(coef);
   const bool glob = L.n_glob == 1;
   const ff xg = glob ? ldx(x, L.glob_col) : ff_zero();
+  const uint64_t pol = policy_evict_first();  // records are read once per product
 
   if (half == 0 && lane == 0) {
 #pragma unroll
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(NP * 64, 1)
       const int64_t r = gp + s * np;
       if (r < L.n_recs) {
         mbar_expect_tx(&bar[s], R::BYTES);
-        tma_load(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s]);
+        tma_load_hint(stage0 + s * R::BYTES, recs + r * R::BYTES, R::BYTES, &bar[s], pol);
       }
     }
 #pragma unroll
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(NP * 64, 1)
         if (rn < L.n_recs) {
           fence_proxy_async();
           mbar_expect_tx(&bar[s], R::BYTES);
-          tma_load(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s]);
+          tma_load_hint(stage0 + s * R::BYTES, recs + rn * R::BYTES, R::BYTES, &bar[s], pol);
         }
         const int64_t rp = rn + A1_PF * np;
         if (rp < L.n_recs) prefetch_l2(recs + rp * R::BYTES, R::BYTES);
@@ -679,7 +681,14 @@ __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
   }
 }
 
-template <bool F32>
+// aprod 2, attitude part. A warp walks its range of start knots s; the rows of
+// knot s are one run of the knot order, read 64 positions at a time (2 per
+// lane): the coefficients in that order (coalesced). u comes from its copy in
+// the same order, or (BLK) from the blocked copy, where the run of knot s is one
+// segment per row block: lane b holds the bounds of block b's segment, and for
+// each 64 positions the warp walks the segments that overlap them, every lane
+// taking the blocked position of its own positions.
+template <bool F32, bool BLK>
 __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __restrict__ y_knot,
                                                     double* __restrict__ x, const double* stop) {
   if (stop && *stop != 0.0) return;
@@ -694,26 +703,69 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) win[a][j] = ff_zero();
   const int64_t K = L.n_knots;
-  // positions per lane per step: 2 keeps the kernel at ~128 registers, so a block
-  // fits beside the instrumental kernel's block on every SM (measured better
-  // than 4 positions at ~180 registers: 30M rows 1.60 -> 1.56 ms for aprod 2)
+  const int64_t kb_w = L.n_knots - 2;
+  const int nb = BLK ? L.n_kblk : 0;
+  const bool own = lane < nb;
+  const int32_t* kbl = BLK ? L.kb_start + (int64_t)(own ? lane : 0) * kb_w : nullptr;
+  // bounds of block `lane`'s segment: the current knot's, the next loaded ahead
+  int e0 = 0, e1 = 0;
+  if (BLK && own) {
+    e0 = kbl[s_begin];
+    e1 = kbl[s_begin + 1];
+  }
+  // positions per lane per step: 2 keeps the kernel near 128 registers, so a
+  // block fits beside the instrumental kernel's block on every SM
   constexpr int U = 2;
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
+    const int total = (int)(p1 - p0);
+    // segment of block `lane`: blocked start a, length n, start c in the run
+    int a = 0, n = 0, c = 0;
+    if constexpr (BLK) {
+      a = e0;
+      n = e1 - e0;
+      e0 = e1;
+      if (own && s + 2 < kb_w) e1 = kbl[s + 2];
+      c = n;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, c, d);
+        if (lane >= d) c += y;
+      }
+      c -= n;
+    }
     ff acc[12];
 #pragma unroll
     for (int t = 0; t < 12; ++t) acc[t] = ff_zero();
-    for (int64_t pb = p0; pb < p1; pb += 32 * U) {
+    int bseg = 0;  // first segment that ends after the current step's start
+    for (int qb = 0; qb < total; qb += 32 * U) {
+      int64_t pu[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) pu[q] = p0 + qb + lane + 32 * q;
+      if constexpr (BLK) {
+        // skip the segments that end at or before qb (some segment ends after it)
+        while (__shfl_sync(0xffffffffu, c + n, bseg) <= qb) ++bseg;
+        for (int b = bseg; b < nb; ++b) {
+          const int cb = __shfl_sync(0xffffffffu, c, b);
+          if (cb >= qb + 32 * U) break;
+          const int nbb = __shfl_sync(0xffffffffu, n, b), ab = __shfl_sync(0xffffffffu, a, b);
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            const int qi = qb + lane + 32 * q;
+            if (qi >= cb && qi < cb + nbb) pu[q] = (int64_t)ab + (qi - cb);
+          }
+        }
+      }
       ff u[U];
       ff v[12][U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        const int64_t p = pb + lane + 32 * q;
-        const bool in = p < p1;
-        const float2 uu = in ? __ldcs(y_knot + p) : make_float2(0.f, 0.f);
+        const int qi = qb + lane + 32 * q;
+        const bool in = qi < total;
+        const float2 uu = in ? __ldcs(y_knot + pu[q]) : make_float2(0.f, 0.f);
         u[q] = ff{uu.x, uu.y};
 #pragma unroll
-        for (int t = 0; t < 12; ++t) v[t][q] = in ? att_val<F32>(L, t, p) : ff_zero();
+        for (int t = 0; t < 12; ++t) v[t][q] = in ? att_val<F32>(L, t, p0 + qi) : ff_zero();
       }
 #pragma unroll
       for (int t = 0; t < 12; ++t) {
@@ -726,9 +778,9 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
     // the windows hold this lane's partial sums; only a finished knot is
     // reduced over the warp (3 values instead of 12 per bucket)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a3 = 0; a3 < 3; ++a3)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) win[a][j] = ff_add(win[a][j], acc[4 * a + j]);
+      for (int j = 0; j < 4; ++j) win[a3][j] = ff_add(win[a3][j], acc[4 * a3 + j]);
     {
       // knot s is complete for this warp
       const ff k0 = ff_warp_sum(win[0][0]), k1 = ff_warp_sum(win[1][0]),
@@ -736,11 +788,11 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
       if (lane < 3) red_ff(x + L.att_base + lane * K + s, lane == 0 ? k0 : lane == 1 ? k1 : k2);
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      win[a][0] = win[a][1];
-      win[a][1] = win[a][2];
-      win[a][2] = win[a][3];
-      win[a][3] = ff_zero();
+    for (int a3 = 0; a3 < 3; ++a3) {
+      win[a3][0] = win[a3][1];
+      win[a3][1] = win[a3][2];
+      win[a3][2] = win[a3][3];
+      win[a3][3] = ff_zero();
     }
   }
   // the three knots after the last bucket also received contributions
@@ -900,12 +952,13 @@ int launch_to_ff(const double* x, const double* scale, const int16_t* cexp, int 
   return cuda_status(cudaGetLastError());
 }
 
-int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
-                      double* guard, cudaStream_t st) {
+int launch_to_ff_knot(gsr_system* sys, int which_values, const double* y, float2* y_ff,
+                      float2* y_knot, double* guard, cudaStream_t st) {
   if (sys->L.n_rows <= 0) return GSR_OK;
   int blocks = (int)((sys->L.n_rows + 255) / 256);
   if (blocks > sys->num_sms * 8) blocks = sys->num_sms * 8;
-  k_to_ff_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_ff, y_knot, guard);
+  k_to_ff_knot<<<blocks, 256, 0, st>>>(sys->L, y, y_ff, y_knot, knot_positions(sys->L, which_values),
+                                       guard);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1006,8 +1059,11 @@ int launch_aprod2(gsr_system* sys, int which_values, const float2* y, const floa
   }
   const int att_blocks = (L.n_att_warps + 7) / 8;
   if (att_blocks > 0) {
-    if (f32) k_aprod2_att<true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
-    else k_aprod2_att<false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    // the float-pair copy of u is blocked when n_kblk > 1; the FP32 one never
+    if (f32) k_aprod2_att<true, false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    else if (L.n_kblk > 1)
+      k_aprod2_att<false, true><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
+    else k_aprod2_att<false, false><<<att_blocks, 256, 0, sys->side>>>(L, y_knot, x, stop);
     if (cudaGetLastError() != cudaSuccess) return GSR_E_CUDA;
   }
   const int ab = (int)std::min<int64_t>((int64_t)sys->num_sms * 8, ((L.n_recs + 1) / 2 + 7) / 8);
@@ -1075,7 +1131,7 @@ static int aprod2_direct_obs(gsr_system* sys, int which_values, const double* y,
   if (sys->wide) return launch_aprod2_f64(sys, which_values, y, 1, x, nullptr, st);
   double* guard = sys->S.guard;
   if (cudaMemsetAsync(guard, 0, sizeof(double), st) != cudaSuccess) return GSR_E_CUDA;
-  int rc = launch_to_ff_knot(sys, y, sys->S.y_ff, sys->S.y_knot, guard, st);
+  int rc = launch_to_ff_knot(sys, which_values, y, sys->S.y_ff, sys->S.y_knot, guard, st);
   if (rc != GSR_OK) return rc;
   double* acc = L.col_exp ? sys->S.zx : x;
   if (L.col_exp &&

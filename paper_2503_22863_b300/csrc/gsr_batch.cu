@@ -331,35 +331,47 @@ __global__ void __launch_bounds__(256, 2) k_aprod2_att_b(Layout L, const float2*
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int i = 0; i < 4; ++i) win[a][i] = ff_zero();
+  const int64_t kb_w = L.n_knots - 2;
+  // the float-pair copy of Y is blocked when n_kblk > 1, the FP32 one never
+  const bool blk = !F32 && L.n_kblk > 1;
+  const int nbk = blk ? L.n_kblk : 1;
   for (int s = s_begin; s < s_end; ++s) {
-    const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
     ff acc[12];
 #pragma unroll
     for (int t = 0; t < 12; ++t) acc[t] = ff_zero();
     constexpr int U = 2;  // positions per stream per step, all loads issued first
-    for (int64_t pb = p0 + q; pb < p1; pb += U * S) {
-      ff u[U];
-      ff v[12][U];
+    // the rows of knot s: one run of the knot order (coefficients, from g0) and
+    // of the copy of Y, or one segment per row block of its blocked copy
+    int64_t g0 = L.knot_start[s];
+    for (int bk = 0; bk < nbk; ++bk) {
+      const int64_t p0 = blk ? L.kb_start[bk * kb_w + s] : g0;
+      const int64_t n = blk ? L.kb_start[bk * kb_w + s + 1] - p0 : L.knot_start[s + 1] - g0;
+      for (int64_t ib = q; ib < n; ib += U * S) {
+        ff u[U];
+        ff v[12][U];
 #pragma unroll
-      for (int i = 0; i < U; ++i) {
-        const int64_t p = pb + (int64_t)i * S;
-        const bool in = p < p1;
-        u[i] = in ? pair_t<F32>(__ldcs(Yk + p * KP + j)) : ff_zero();
+        for (int i = 0; i < U; ++i) {
+          const int64_t k = ib + (int64_t)i * S;
+          const bool in = k < n;
+          const int64_t p = p0 + k, g = g0 + k;
+          u[i] = in ? pair_t<F32>(__ldcs(Yk + p * KP + j)) : ff_zero();
+#pragma unroll
+          for (int t = 0; t < 12; ++t) {
+            if constexpr (F32)
+              v[t][i] = ff{in ? __ldg(L.att_knot_f32 + (int64_t)t * L.n_rows + g) : 0.0f, 0.0f};
+            else
+              v[t][i] = in ? ldf(L.att_knot_ff + (int64_t)t * L.n_rows + g) : ff_zero();
+          }
+        }
 #pragma unroll
         for (int t = 0; t < 12; ++t) {
-          if constexpr (F32)
-            v[t][i] = ff{in ? __ldg(L.att_knot_f32 + (int64_t)t * L.n_rows + p) : 0.0f, 0.0f};
-          else
-            v[t][i] = in ? ldf(L.att_knot_ff + (int64_t)t * L.n_rows + p) : ff_zero();
+          ff sum = mul_t<F32>(v[t][0], u[0]);
+#pragma unroll
+          for (int i = 1; i < U; ++i) sum = fma_t<F32>(v[t][i], u[i], sum);
+          acc[t] = add_t<F32>(acc[t], sum);
         }
       }
-#pragma unroll
-      for (int t = 0; t < 12; ++t) {
-        ff sum = mul_t<F32>(v[t][0], u[0]);
-#pragma unroll
-        for (int i = 1; i < U; ++i) sum = fma_t<F32>(v[t][i], u[i], sum);
-        acc[t] = add_t<F32>(acc[t], sum);
-      }
+      g0 += n;
     }
 #pragma unroll
     for (int t = 0; t < 12; ++t)
@@ -622,8 +634,9 @@ __global__ void __launch_bounds__(256) k_maxexp_b(const double* __restrict__ B, 
 template <int KP>
 __global__ void __launch_bounds__(256) k_init_b(Layout L, const double* __restrict__ B, int k,
                                                 const int* bexp, float2* __restrict__ U,
-                                                float2* __restrict__ Uk, double* sc, double* part,
-                                                unsigned int* counter) {
+                                                float2* __restrict__ Uk,
+                                                const int32_t* __restrict__ kp, double* sc,
+                                                double* part, unsigned int* counter) {
   __shared__ double tot[32];
   double s2 = 0.0;
   const int jt = (int)(threadIdx.x % KP);
@@ -636,7 +649,7 @@ __global__ void __launch_bounds__(256) k_init_b(Layout L, const double* __restri
     const double v = j < k ? ldexp(B[i * k + j], -sb) : 0.0;
     const ff f = ff_from_double(v);
     U[e] = make_float2(f.h, f.l);
-    Uk[(int64_t)L.pos[i] * KP + j] = make_float2(f.h, f.l);
+    Uk[(int64_t)kp[i] * KP + j] = make_float2(f.h, f.l);
     s2 = __fma_rn(v, v, s2);
   }
   if (grid_sum_kv<KP, 1>(&s2, part, counter, tot) && threadIdx.x < KP)
@@ -1200,10 +1213,11 @@ static int enqueue_iter_b(gsr_system* s, BatchWork* w, const double* xref, const
 }
 template <int KP>
 static int init_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool f32) {
   const int64_t rb = std::min<int64_t>((s->L.n_rows * KP + 255) / 256, (int64_t)s->num_sms * 8);
-  k_init_b<KP><<<(int)std::max<int64_t>(rb, 1), 256, 0, st>>>(s->L, B, k, s->S.iexp, w->U, w->Uk,
-                                                              w->sc, w->part, w->count + 3);
+  k_init_b<KP><<<(int)std::max<int64_t>(rb, 1), 256, 0, st>>>(
+      s->L, B, k, s->S.iexp, w->U, w->Uk,
+      knot_positions(s->L, f32 ? GSR_VALUES_F32 : GSR_VALUES_F64), w->sc, w->part, w->count + 3);
   if (xref) {
     const int vb = (int)std::min<int64_t>((s->L.n_unk * KP + 255) / 256, (int64_t)s->num_sms * 8);
     k_xref2_b<KP><<<vb, 256, 0, st>>>(s->L.n_unk, xref, w->sc, w->part, w->count + 4);
@@ -1211,8 +1225,8 @@ static int init_b(gsr_system* s, BatchWork* w, const double* B, int k, const dou
   return cuda_status(cudaGetLastError());
 }
 static int init_iter_b(gsr_system* s, BatchWork* w, const double* B, int k, const double* xref,
-                       cudaStream_t st) {
-  GSR_KP_DISPATCH(w->KP, (init_b<KP>(s, w, B, k, xref, st)));
+                       cudaStream_t st, bool f32) {
+  GSR_KP_DISPATCH(w->KP, (init_b<KP>(s, w, B, k, xref, st, f32)));
 }
 
 __global__ void k_pack_xref(const double* __restrict__ in, int k, int KP, int64_t n,
@@ -1292,7 +1306,7 @@ static int lsqr_batch_run(gsr_system* s, int k, const double* B, double* X,
     k_pack_xref<<<vb, 256, 0, st>>>(o->x_ref, k, KP, m, xref);
   }
   if (e != cudaSuccess) return GSR_E_CUDA;
-  rc = init_iter_b(s, w, B, k, xref, st);
+  rc = init_iter_b(s, w, B, k, xref, st, f32);
   if (rc == GSR_OK) rc = enqueue_iter_b(s, w, xref, xoff, err_dev, st, 1, f32);
   if (rc != GSR_OK) return rc;
   int64_t n_launches = 12;

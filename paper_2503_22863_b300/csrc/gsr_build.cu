@@ -36,7 +36,8 @@ __device__ __forceinline__ void put_indices(unsigned char* rec, int l, int c, in
 }
 
 // Lay out rows [r0, r0+n) of the raw upload into the records and the
-// knot-ordered attitude copy, each value rescaled to 2^(e_i + g_j) A_ij when
+// knot-ordered attitude copy (row r at L.gpos[r]; the FP32 records carry that
+// position, the float-pair ones L.pos[r]), each value rescaled to 2^(e_i + g_j) A_ij when
 // the system has exponents; accumulate the squared column norms of 2^g_j A_ij.
 __global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
                          unsigned char* __restrict__ rec_f32, float2* __restrict__ att_ff,
@@ -49,12 +50,12 @@ __global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
     const int64_t r = r0 + i;
     const int64_t rec = r / REC_ROWS;
     const int l = (int)((r % REC_ROWS) >> 1), c = (int)(r & 1);
-    const int st = star[r], sk = s_knot[r], p = L.pos[r];
+    const int st = star[r], sk = s_knot[r], p = L.pos[r], gp = L.gpos[r];
     const int er = L.row_exp ? (int)L.row_exp[r] : 0;
     unsigned char* rf = rec_ff + rec * Rec<false>::BYTES;
     unsigned char* r32 = rec_f32 ? rec_f32 + rec * Rec<true>::BYTES : nullptr;
     put_indices<false>(rf, l, c, st, sk, p, raw_instr + i * 6);
-    if (r32) put_indices<true>(r32, l, c, st, sk, p, raw_instr + i * 6);
+    if (r32) put_indices<true>(r32, l, c, st, sk, gp, raw_instr + i * 6);
     for (int t = 0; t < NSLOT; ++t) {
       double v = raw[i * NSLOT + t];
       int64_t col = -1;
@@ -79,8 +80,8 @@ __global__ void k_layout(Layout L, unsigned char* __restrict__ rec_ff,
       pf[2 * c + 1] = lo;
       if (r32) reinterpret_cast<float*>(r32 + slot_offset<true>(t) + l * 8)[c] = h;
       if (t >= 5 && t < 17) {
-        att_ff[(int64_t)(t - 5) * L.n_rows + p] = make_float2(h, lo);
-        if (att_f32) att_f32[(int64_t)(t - 5) * L.n_rows + p] = h;
+        att_ff[(int64_t)(t - 5) * L.n_rows + gp] = make_float2(h, lo);
+        if (att_f32) att_f32[(int64_t)(t - 5) * L.n_rows + gp] = h;
       }
       if (col < 0) continue;
       const double vc = ec ? ldexp(v, ec) : v;
@@ -128,7 +129,7 @@ void free_system(gsr_system* s) {
   free_constraints(s);
   delete[] s->colnorm_obs;
   void* ptrs[] = {s->rec_ff, s->rec_f32, s->pos, s->att_knot_ff, s->att_knot_f32, s->knot_start,
-                  s->att_warp_knot, s->iseg, s->ient_ff, s->ient_f32,
+                  s->kb_start, s->gpos, s->att_warp_knot, s->iseg, s->ient_ff, s->ient_f32,
                   s->ient_key, s->colnorm, s->u, s->u_knot, s->v, s->w, s->xz, s->z,
                   s->dscale, s->dscale_ff, s->v_ff, s->mx_x1, s->mx_d, s->mx_r, s->scal, s->S.red,
                   s->S.count, s->S.x_ff, s->S.x3,
@@ -520,14 +521,44 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
     const int r = choose_rescaling(d, vals, star.data(), s_knot.data(), instr, nt, rs);
     if (r != GSR_OK) return r;
   }
-  // ---- counting sort of rows by start knot (stable) ----
+  // ---- knot order: counting sort of rows by start knot (stable), and the
+  // blocked order of the float-pair copy of u ----
   const int64_t n_buckets = d.n_knots - 3;
-  std::vector<int64_t> knot_start(n_buckets + 1, 0);
+  std::vector<int64_t> knot_start(n_buckets + 1, 0);  // first position of start knot s
   for (int64_t r = 0; r < n; ++r) knot_start[s_knot[r] + 1]++;
   for (int64_t b = 0; b < n_buckets; ++b) knot_start[b + 1] += knot_start[b];
+  std::vector<int32_t> gpos(n);  // position of each row in the knot order
   {
     std::vector<int64_t> next(knot_start.begin(), knot_start.end() - 1);
-    for (int64_t r = 0; r < n; ++r) pos[r] = (int32_t)(next[s_knot[r]]++);
+    for (int64_t r = 0; r < n; ++r) gpos[r] = (int32_t)(next[s_knot[r]]++);
+  }
+  // blocked copy of u (see KBLK_MAX): n_kblk blocks of kblk_rows rows
+  int64_t n_kblk = std::min<int64_t>(KBLK_MAX, n / (KBLK_MIN_PER_KNOT *
+                                                    std::max<int64_t>(1, n_buckets)));
+  int64_t kblk_rows = n;
+  if (n_kblk >= 2) {
+    kblk_rows = ((n + n_kblk - 1) / n_kblk + REC_ROWS - 1) / REC_ROWS * REC_ROWS;
+    n_kblk = (n + kblk_rows - 1) / kblk_rows;
+  }
+  if (n_kblk < 2 || kblk_rows > KBLK_MAX_ROWS) {
+    n_kblk = 1;
+    kblk_rows = n;
+  }
+  const int64_t kb_w = n_buckets + 1;
+  std::vector<int32_t> kb_start;
+  if (n_kblk > 1) {
+    kb_start.assign((size_t)n_kblk * kb_w, 0);
+    for (int64_t b = 0; b < n_kblk; ++b) {
+      const int64_t r0 = b * kblk_rows, r1 = std::min<int64_t>(n, r0 + kblk_rows);
+      int32_t* ks = kb_start.data() + b * kb_w;
+      for (int64_t r = r0; r < r1; ++r) ks[s_knot[r] + 1]++;
+      ks[0] = (int32_t)r0;
+      for (int64_t k = 0; k < n_buckets; ++k) ks[k + 1] += ks[k];
+      std::vector<int32_t> next(ks, ks + n_buckets);
+      for (int64_t r = r0; r < r1; ++r) pos[r] = next[s_knot[r]]++;
+    }
+  } else {
+    std::copy(gpos.begin(), gpos.end(), pos.begin());
   }
   // ---- instrumental tiles and column groups ----
   // Larger tiles mean fewer tile switches per entry. The columns are split
@@ -621,6 +652,10 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   A(dalloc(&sys->att_knot_ff, (size_t)n * 12));
   if (want_f32) A(dalloc(&sys->att_knot_f32, (size_t)n * 12));
   A(dalloc(&sys->knot_start, (size_t)n_buckets + 1));
+  if (n_kblk > 1) {
+    A(dalloc(&sys->kb_start, kb_start.size()));
+    A(dalloc(&sys->gpos, (size_t)n));
+  }
   A(dalloc(&sys->att_warp_knot, (size_t)L.n_att_warps + 1));
   A(dalloc(&sys->iseg, ir.seg.size()));
   A(dalloc(&sys->ient_key, n_ent));
@@ -686,6 +721,11 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   C(cudaMemcpyAsync(sys->pos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->knot_start, knot_start.data(), (size_t)(n_buckets + 1) * 8,
                     cudaMemcpyHostToDevice, st));
+  if (n_kblk > 1) {
+    C(cudaMemcpyAsync(sys->kb_start, kb_start.data(), kb_start.size() * 4,
+                      cudaMemcpyHostToDevice, st));
+    C(cudaMemcpyAsync(sys->gpos, gpos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+  }
   C(cudaMemcpyAsync(sys->att_warp_knot, att_warp_knot.data(), (size_t)(L.n_att_warps + 1) * 4,
                     cudaMemcpyHostToDevice, st));
   C(cudaMemcpyAsync(sys->iseg, ir.seg.data(), ir.seg.size() * sizeof(longlong2),
@@ -702,6 +742,10 @@ int build_system(const gsr_dims* dims, const double* vals, const int64_t* astro_
   L.att_knot_ff = sys->att_knot_ff;
   L.att_knot_f32 = sys->att_knot_f32;
   L.knot_start = sys->knot_start;
+  L.kb_start = sys->kb_start;
+  L.gpos = n_kblk > 1 ? sys->gpos : sys->pos;
+  L.n_kblk = (int32_t)n_kblk;
+  L.kblk_rows = kblk_rows;
   L.att_warp_knot = sys->att_warp_knot;
   L.iseg = sys->iseg;
   L.ient_ff = sys->ient_ff;

@@ -37,6 +37,15 @@ __host__ __device__ constexpr int64_t instr_smem_bytes(int64_t ct_rows, int64_t 
   return nbuf * instr_tile_bytes(ct_rows, max_ent, f32) + hist_bins * 8;
 }
 // Two blocks of the instrumental kernel share an SM when each fits this much.
+// Row blocks of the blocked knot order of u: as many as keep at least
+// KBLK_MIN_PER_KNOT rows per (block, knot) on average, at most KBLK_MAX (the
+// attitude kernel walks one segment per block and knot, one block per lane),
+// and blocked at all only when that gives at least 2 blocks of at most
+// KBLK_MAX_ROWS rows (the slice of u a block scatters into must stay well
+// inside L2: 8 B per row).
+constexpr int KBLK_MAX = 32;
+constexpr int64_t KBLK_MIN_PER_KNOT = 16;
+constexpr int64_t KBLK_MAX_ROWS = 1 << 21;
 constexpr int INSTR_SMEM_HALF = 112 * 1024;
 
 // ---------------------------------------------------------------------------
@@ -224,6 +233,22 @@ __device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// The same copy with an L2 eviction-priority policy (createpolicy). Data read
+// once per product (the row records) is marked evict-first, so that L2 keeps the
+// lines that are reused: gathered unknowns and partly written output sectors.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tma_load_hint(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
 // Hint: start moving bytes [src, src + bytes) from DRAM into L2 (no
 // completion to wait for; 16-byte aligned address, size a multiple of 16).
 __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
@@ -266,11 +291,27 @@ struct Layout {
   int64_t att_base, instr_base, glob_col;
   const unsigned char* rec_ff;          // n_recs x Rec<false>::BYTES
   const unsigned char* rec_f32;         // n_recs x Rec<true>::BYTES, or null
-  const int32_t* pos;                   // [n_rows] knot-order position of each row
-  // attitude coefficients in knot order (rows stably sorted by start knot s)
-  const float2* att_knot_ff;            // [t][n_rows], t = 4*axis + j
+  // Knot order: rows sorted by start knot s, stably (the rows of a knot in row
+  // order); the attitude coefficients and the FP32-phase copies of u use it
+  // (position gpos). When n_kblk > 1 the float-pair copy of u is blocked
+  // instead (position pos): the rows are cut into n_kblk blocks of kblk_rows
+  // consecutive rows and sorted by s inside each block, so that aprod 1, which
+  // walks the rows in order, scatters u into one block's slice at a time (a
+  // slice L2 holds while its sectors fill). Inside knot s the two orders agree:
+  // the rows of s in block 0, then block 1, ...
+  const int32_t* pos;                   // [n_rows] position of each row in the float-pair
+                                        // copy of u (blocked when n_kblk > 1)
+  const int32_t* gpos;                  // [n_rows] position in the knot order (== pos when
+                                        // n_kblk == 1)
+  const float2* att_knot_ff;            // [t][n_rows] in the knot order, t = 4*axis + j
   const float* att_knot_f32;            // [t][n_rows] FP32 copy (or null)
+  const int32_t* kb_start;              // [n_kblk][n_knots - 2] first blocked position of
+                                        // start knot s in block b (entry n_knots - 3: the
+                                        // block's end); null when n_kblk == 1
+  int32_t n_kblk;                       // row blocks (1: not blocked; at most KBLK_MAX)
+  int64_t kblk_rows;                    // rows per block (a multiple of 64)
   const int64_t* knot_start;            // [n_knots - 3 + 1] first position of start knot s
+                                        // in the knot order (rows with start knot < s)
   const int32_t* att_warp_knot;         // [n_att_warps + 1] start-knot range of each warp
   int32_t n_att_warps;
   // instrumental entries of each tile of ct_rows rows, in rounds of distinct bins
@@ -294,6 +335,12 @@ struct Layout {
   const int16_t* row_exp;               // [n_rows] e_i
   const int16_t* col_exp;               // [n_unk]  g_j
 };
+
+// Positions of the knot-order copy of u that the products with FP32 values
+// (FP32 records) or float-pair values read.
+__host__ __device__ inline const int32_t* knot_positions(const Layout& L, int which_values) {
+  return which_values == GSR_VALUES_F32 ? L.gpos : L.pos;
+}
 
 struct Scratch {
   double* red;          // partial-sum slots for last-block reductions

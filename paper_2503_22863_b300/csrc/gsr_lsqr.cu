@@ -173,9 +173,9 @@ __device__ __forceinline__ int b_exponent(const int* mx) {
 // Start: u~ = 2^-s b (and its knot-order copy), ||u~||^2.
 // ---------------------------------------------------------------------------
 __global__ void k_init_u(Layout L, const double* __restrict__ b, const int* bexp,
-                         float2* __restrict__ u, float2* __restrict__ u_knot, double* scal,
-                         double* part, unsigned int* counter) {
-  const int32_t* pos = L.pos;
+                         float2* __restrict__ u, float2* __restrict__ u_knot,
+                         const int32_t* __restrict__ pos, double* scal, double* part,
+                         unsigned int* counter) {
   const int sb = b_exponent(bexp);
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BEXP] = sb;
   double s2 = 0.0, z0 = 0.0, z1 = 0.0;
@@ -613,8 +613,8 @@ int lsqr_run(gsr_system* s, const double* b, double* x, const gsr_lsqr_opts* o,
   if (o->var) k_zero<<<vb, 256, 0, st>>>(L.n_unk, o->var, nullptr);
   k_zero<<<vb, 256, 0, st>>>(L.n_unk, reinterpret_cast<double*>(s->xz), nullptr);
   // start: beta_1 u_1 = b, alpha_1 v_1 = (A D)^T u_1, w_1 = v_1, x_0 = 0
-  k_init_u<<<rb, 256, 0, st>>>(L, b, s->S.iexp, s->u, s->u_knot, scal, s->S.red,
-                               s->S.count + 4);
+  k_init_u<<<rb, 256, 0, st>>>(L, b, s->S.iexp, s->u, s->u_knot, knot_positions(L, which_values),
+                               scal, s->S.red, s->S.count + 4);
   int rc = con_init_lsqr(s, b + L.n_rows, scal + S_BEXP, scal + S_UNORM2, st);
   if (rc != GSR_OK) return rc;
   k_zero<<<vb, 256, 0, st>>>(L.n_unk, s->z, nullptr);

@@ -18,6 +18,8 @@ struct gsr_system {
   float2* att_knot_ff;
   float* att_knot_f32;
   int64_t* knot_start;
+  int32_t* kb_start;
+  int32_t* gpos;  // null when the knot order is not blocked (L.gpos == pos)
   int32_t* att_warp_knot;
   longlong2* iseg;
   float2* ient_ff;
@@ -136,9 +138,10 @@ int launch_to_ff(const double* x, const double* scale, const int16_t* cexp, int 
 // Interleave the attitude part of a float-pair aprod 1 input by start knot
 // (into sys->S.x3); aprod 1 reads it with three 32-byte loads per row.
 int launch_att_x3(gsr_system* sys, const float2* x_ff, const double* stop, cudaStream_t st);
-// y (double) -> y_ff (row order) and y_knot (knot order) as float pairs.
-int launch_to_ff_knot(gsr_system* sys, const double* y, float2* y_ff, float2* y_knot,
-                      double* guard, cudaStream_t st);
+// y (double) -> y_ff (row order) and y_knot (the knot-order copy the products
+// with `which_values` read) as float pairs.
+int launch_to_ff_knot(gsr_system* sys, int which_values, const double* y, float2* y_ff,
+                      float2* y_knot, double* guard, cudaStream_t st);
 int cuda_status(cudaError_t e);
 int set_kernel_attributes();
 void destroy_batch(gsr_system* s);

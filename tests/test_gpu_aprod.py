@@ -2,7 +2,9 @@
 
 Element by element on seeded systems: the tiny 100,000-row workload, ragged
 small shapes (partial last tile, single star, minimum knots and instrumental
-columns, no global column, stars spanning lanes, tiles and warp ranges), and
+columns, no global column, stars spanning lanes, tiles and warp ranges; the
+knot-order copy of u blocked by rows, up to 32 blocks with a partial last
+one, or not blocked), and
 the full 30M-row workload in the bench's launch configuration. The bar:
 max |gpu - oracle| / max (|A||x|) <= 1e-12 (aprod 1) and the
 same with |A|^T|y| (aprod 2)."""
@@ -26,6 +28,8 @@ SHAPES = [
     dict(n_stars=5, obs=3000, poisson=False, n_knots=5000, n_instr=20000, n_glob=1, seed=6),
     # the most instrumental columns (split into two column groups), many tiles
     dict(n_stars=20000, obs=30, poisson=True, n_knots=3000, n_instr=24576, n_glob=1, seed=7),
+    # few knots: the float-pair copy of u in the most row blocks (32, the last partial)
+    dict(n_stars=5000, obs=40, poisson=True, n_knots=50, n_instr=100, n_glob=1, seed=8),
 ]
 
 
