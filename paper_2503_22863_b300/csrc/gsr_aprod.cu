@@ -664,13 +664,14 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : 2)
 }
 
 // ---------------------------------------------------------------------------
-// aprod 2, attitude part over the knot-sorted copy: a warp walks its range of
-// start knots; positions with start knot s add into knots s..s+3 of each
-// axis. A sliding 4-knot window per axis of per-lane partial sums lives in
-// registers; knot s is final (for this warp) once bucket s is done, and is
-// then summed over the warp and added into x. Every load of a step (U
-// positions per lane) is issued before any arithmetic.
+// aprod 2, attitude part over the knot-ordered copies: positions with start
+// knot s add into knots s..s+3 of each axis. A sliding 4-knot window per axis
+// of per-lane partial sums lives in registers; knot s is final (for the warp)
+// once its positions are done, and is then summed over the warp and added into
+// x. Every load of a step (U positions per lane) is issued before any
+// arithmetic.
 // ---------------------------------------------------------------------------
+// Attitude coefficient t of knot-order position p.
 template <bool F32>
 __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
   if constexpr (F32) {
@@ -681,9 +682,9 @@ __device__ __forceinline__ ff att_val(const Layout& L, int t, int64_t p) {
   }
 }
 
-// aprod 2, attitude part. A warp walks its range of start knots s; the rows of
-// knot s are one run of the knot order, read 64 positions at a time (2 per
-// lane): the coefficients in that order (coalesced). u comes from its copy in
+// A warp walks its range of start knots s; the rows of knot s are one run of
+// the knot order, read 64 positions at a time (2 per lane): the coefficients
+// in that order (coalesced). u comes from its copy in
 // the same order, or (BLK) from the blocked copy, where the run of knot s is one
 // segment per row block: lane b holds the bounds of block b's segment, and for
 // each 64 positions the warp walks the segments that overlap them, every lane
@@ -900,11 +901,11 @@ __global__ void k_add_rescaled(int64_t n, const double* __restrict__ z,
 constexpr int A1_NP = 6;                    // warp pairs per aprod 1 block (one block per SM)
 constexpr int A1_NS_FF = 2, A1_NS_F32 = 3;  // record buffers per warp pair
 constexpr int A1_XI_SMEM_MAX = 6144;        // instrumental unknowns staged in shared memory
-// More instrumental unknowns than that, float-pair values: one record buffer
-// per pair and five pairs, so that all of them still fit beside the buffers
-// (up to ~20,000; measured on 160M rows x 20,000 columns: 12.06 -> 11.74 ms;
-// with FP32 values the same idea, 8 pairs, was slower)
-constexpr int A1_NP1_FF = 5;
+// More instrumental unknowns than that: one record buffer per pair and five
+// pairs, so that all of them still fit beside the buffers (up to ~20,000 with
+// float-pair values; measured on 160M rows x 20,000 columns: 12.06 -> 11.74 ms,
+// and with FP32 values, which gathered them through L2 before, 8.47 -> 6.31 ms)
+constexpr int A1_NP1 = 5;
 constexpr int A1_SMEM_MAX = 226 * 1024;  // dynamic shared memory of that configuration
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSR_OK : GSR_E_CUDA; }
@@ -931,8 +932,9 @@ int set_kernel_attributes() {
 #define GSR_A1W_ATTR(F, YF, X3, NP)                                                       \
   C(cudaFuncSetAttribute(k_aprod1<F, YF, X3, NP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          A1_SMEM_MAX));
-  GSR_A1W_ATTR(false, true, true, A1_NP1_FF) GSR_A1W_ATTR(false, false, true, A1_NP1_FF)
-  GSR_A1W_ATTR(false, false, false, A1_NP1_FF)
+  GSR_A1W_ATTR(false, true, true, A1_NP1) GSR_A1W_ATTR(false, false, true, A1_NP1)
+  GSR_A1W_ATTR(false, false, false, A1_NP1) GSR_A1W_ATTR(true, true, true, A1_NP1)
+  GSR_A1W_ATTR(true, false, true, A1_NP1) GSR_A1W_ATTR(true, false, false, A1_NP1)
 #undef GSR_A1W_ATTR
 #define GSR_INSTR_ATTR(F, B, T)                                                             \
   C(cudaFuncSetAttribute(k_aprod2_instr<F, B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -981,14 +983,20 @@ static int launch_aprod1_t(gsr_system* sys, int which_values, const float2* x_ff
     return GSR_OK;
   }
   const bool f32 = which_values == GSR_VALUES_F32;
-  const int64_t smem1 = (int64_t)A1_NP1_FF * Rec<false>::BYTES + L.n_instr * 8;
-  if (!f32 && L.n_instr > A1_XI_SMEM_MAX && smem1 <= A1_SMEM_MAX) {
-    // A1_NP1_FF pairs with one buffer each, every instrumental unknown staged
-    const int64_t need1 = (L.n_recs + A1_NP1_FF - 1) / A1_NP1_FF;
+  const int64_t smem1 =
+      (int64_t)A1_NP1 * (f32 ? Rec<true>::BYTES : Rec<false>::BYTES) + L.n_instr * 8;
+  if (L.n_instr > A1_XI_SMEM_MAX && smem1 <= A1_SMEM_MAX) {
+    // A1_NP1 pairs with one buffer each, every instrumental unknown staged
+    const int64_t need1 = (L.n_recs + A1_NP1 - 1) / A1_NP1;
     const int b1 = need1 < sys->num_sms ? (int)need1 : sys->num_sms;
-    k_aprod1<false, YFF, X3, A1_NP1_FF, 1><<<b1, A1_NP1_FF * 64, (int)smem1, st>>>(
-        L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count, norm_slot,
-        stop, 1);
+    if (f32)
+      k_aprod1<true, YFF, X3, A1_NP1, 1><<<b1, A1_NP1 * 64, (int)smem1, st>>>(
+          L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+          norm_slot, stop, 1);
+    else
+      k_aprod1<false, YFF, X3, A1_NP1, 1><<<b1, A1_NP1 * 64, (int)smem1, st>>>(
+          L, x_ff, sys->S.x3, y, coef_dev, coef_host, y_knot, sys->S.red, sys->S.count,
+          norm_slot, stop, 1);
     return cuda_status(cudaGetLastError());
   }
   int blocks = sys->num_sms;
