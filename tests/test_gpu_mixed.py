@@ -72,3 +72,18 @@ def test_fp32_phase_alone_is_fp32_accurate(gsr, tiny):
     ref32 = oracle.lsqr(sys32, b, atol=1e-14, btol=1e-14)
     d = relerr(ref32["x"], ref["x"])
     assert 1e-9 < d < 1e-5, d
+
+
+def test_many_instrumental_columns_both_phases(gsr):
+    # 10,000 instrumental columns: more than aprod 1 stages beside two record
+    # buffers per warp pair, so both precisions run its one-buffer configuration
+    # with all of them in shared memory (LSQR form with the knot-order copy)
+    sys = synth.make_system(n_stars=8000, obs=40, poisson=True, n_knots=400, n_instr=10000,
+                            n_glob=1, seed=91)
+    b = rhs(sys)
+    ref = oracle.lsqr(sys, b, atol=1e-14, btol=1e-14)
+    with gsr.System(sys, storage="f32+f64") as S:
+        r64 = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14)
+        assert relerr(to_host(r64["x"]), ref["x"]) <= LSQR_TOL
+        rm = S.lsqr(to_dev(b), atol=1e-14, btol=1e-14, precision="mixed")
+        assert relerr(to_host(rm["x"]), ref["x"]) <= LSQR_TOL
