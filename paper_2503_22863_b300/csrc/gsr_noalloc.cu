@@ -3,12 +3,11 @@
 // library or the caller.
 //
 // Who needs it: code that must not allocate device memory at the moment it
-// calls us. Typical cases are a host loop that is being captured into a CUDA
-// graph (cudaMalloc is not a capturable operation), a process whose device
-// memory has been taken up front by another framework's caching allocator,
-// and latency-critical loops where the implicit device synchronisation of
-// cudaMalloc/cudaFree is not acceptable. This entry point calls no cudaMalloc,
-// cudaFree or any allocating routine; the caller only passes x and y.
+// calls us. Typical cases are a process whose device memory has been taken up
+// front by another framework's caching allocator, and latency-critical loops
+// where the implicit device synchronisation of cudaMalloc/cudaFree is not
+// acceptable. This entry point calls no cudaMalloc, cudaFree or any allocating
+// routine; the caller only passes x and y.
 //
 // The scratch is the float-pair copy of x that the aprod 1 kernel gathers from.
 // It holds at most GSR_NOALLOC_MAX_UNK unknowns (8 MiB of float pairs), a size
