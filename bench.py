@@ -74,7 +74,9 @@ def profiled_traffic(kernel, n_rows):
     figures in profiles/traffic.json, taken on the current kernel source (else
     None): a capture of this very workload when there is one, otherwise a
     smaller workload's bytes per row scaled to n_rows (the traffic of these
-    row-streaming kernels grows about in proportion to the rows processed)."""
+    row-streaming kernels grows about in proportion to the rows processed).
+    A workload with a capture of its own taken on an older source gets None:
+    its own figures showed that the scaled ones do not hold for it."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -85,6 +87,8 @@ def profiled_traffic(kernel, n_rows):
     for e in cur:
         if e.get("n_rows") == n_rows and "bytes_per_launch" in e:
             return float(e["bytes_per_launch"])
+    if any(e.get("kernel") == kernel and e.get("n_rows") == n_rows for e in entries):
+        return None
     for e in cur:
         if "bytes_per_row" in e:
             return float(e["bytes_per_row"]) * n_rows

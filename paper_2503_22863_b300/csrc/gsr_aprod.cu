@@ -714,9 +714,10 @@ __global__ void __launch_bounds__(256) k_aprod2_att(Layout L, const float2* __re
     e0 = kbl[s_begin];
     e1 = kbl[s_begin + 1];
   }
-  // positions per lane per step: 2 keeps the kernel near 128 registers, so a
-  // block fits beside the instrumental kernel's block on every SM
-  constexpr int U = 2;
+  // positions per lane per step: 2 keeps the float-pair kernel near 128
+  // registers, so a block fits beside the instrumental kernel's block on every
+  // SM; the FP32-value kernel stays at 128 registers with 3
+  constexpr int U = F32 ? 3 : 2;
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t p0 = L.knot_start[s], p1 = L.knot_start[s + 1];
     const int total = (int)(p1 - p0);

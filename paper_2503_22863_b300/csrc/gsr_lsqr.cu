@@ -32,12 +32,13 @@ enum Scal {
   S_COUNT
 };
 
-// Grid of the vector kernels: two blocks per SM. Their grid-wide sums end in
-// one atomic per block and a last-block pass over the partials, which costs
-// more than the extra memory parallelism of larger grids gains (measured on
-// 5.16M unknowns: 0.184 ms per iteration at 8 blocks per SM, 0.163 at 4,
-// 0.136 at 2, 0.171 at 1).
-constexpr int RED_BLOCKS = 148 * 2;
+// Grid of the vector kernels: three blocks per SM (their 72 and 80 registers
+// per thread allow three 256-thread blocks). Their grid-wide sums end in one
+// atomic per block and a last-block pass over the partials, which costs more
+// than the extra memory parallelism of larger grids gains (measured on 5.16M
+// unknowns: 0.184 ms per iteration at 8 blocks per SM, 0.163 at 4, 0.171 at 1;
+// 0.143 at 2 against 0.137 at 3, back to back on the current kernels).
+constexpr int RED_BLOCKS = 148 * 3;
 constexpr int VEC_U = 4;             // elements per thread per step of the vector kernels
 
 __device__ __forceinline__ double block_sum3(double& a, double& b, double& c, double* sh) {

@@ -64,3 +64,15 @@ def test_stale_summaries_give_none(tmp_path, monkeypatch):
     _use(tmp_path, monkeypatch, h)
     assert bench.profiled_traffic("aprod1", 1000) is None
     assert bench.profiled_traffic("aprod2", 5) is None
+
+
+def test_stale_capture_of_the_workload_is_not_replaced_by_scaling(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    _write_profiles(tmp_path, h)
+    entries = json.loads((tmp_path / "profiles" / "traffic.json").read_text())
+    entries["entries"].append({"kernel": "aprod1", "workload": "large", "n_rows": 5000,
+                               "bytes_per_launch": 9e6, "kernel_source_hash": "0123456789abcdef"})
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(entries))
+    _use(tmp_path, monkeypatch, h)
+    assert bench.profiled_traffic("aprod1", 5000) is None
+    assert bench.profiled_traffic("aprod2", 5000) == 250.0 * 5000
