@@ -465,8 +465,11 @@ def run_ours(args):
 
     sys_ = make_workload(args.workload)
     t0 = time.perf_counter()
+    free0 = torch.cuda.mem_get_info(local)[0]
     S = gsr.System(sys_, device=local, storage="f32+f64" if args.variants else "f64")
-    log("gsr_create: %.1f s" % (time.perf_counter() - t0))
+    # device memory the system took (its layout, copies and solver vectors)
+    resident_gb = (free0 - torch.cuda.mem_get_info(local)[0]) / 1e9
+    log("gsr_create: %.1f s, %.1f GB on the device" % (time.perf_counter() - t0, resident_gb))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
 
@@ -573,7 +576,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, sys_), "n_rows": n_rows,
                    "n_unk": n_unk, "iterations_to_1e9": n_star, "final_rel_err": err,
-                   "l2": "inputs larger than L2 (system ~11.5 GB resident in HBM)",
+                   "l2": ("inputs larger than L2 (system %.1f GB resident in HBM)" if resident_gb > 0.126
+                          else "system of %.1f GB: fits in L2 (timings not HBM-bound)") % resident_gb,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
