@@ -31,9 +31,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LSQR time-to-1e-9 and aprod1/aprod2 HBM GB/s vs peak: FP64 vs mixed/batched"
 TARGET_ERR = 1e-9
-# Iterations to 1e-9 on the medium workload, measured by this benchmark's own
-# N* search (used by the CPU reference arm, which cannot afford to find N*).
-MEDIUM_ITERS_TO_1E9 = 68
+# Iterations to 1e-9 per workload, measured by this benchmark's own N* search
+# on the GPU (used by the CPU reference arm, which cannot afford to find N*).
+ITERS_TO_1E9 = {"tiny": 25, "small": 51, "medium": 68, "large_small": 40, "large": 45}
 FALLBACK_HBM_GBS = 6400.0
 # Algorithmic bytes of one launch group, per row and per unknown, for the
 # FP64 method: a row is 24 FP64 values + 8 B star offset + 8 B attitude offset
@@ -217,7 +217,7 @@ def run_reference(args):
     b = np.zeros(sys_["n_rows"])
     oracle.aprod1(sys_, sys_["x_star"], b)
     b += sys_["noise"]
-    iters = MEDIUM_ITERS_TO_1E9 if args.workload == "medium" else 40
+    iters = ITERS_TO_1E9[args.workload]
     t0 = time.perf_counter()
     oracle.lsqr(sys_, b, atol=0.0, btol=0.0, conlim=0.0, itnlim=1)
     t1 = time.perf_counter() - t0
