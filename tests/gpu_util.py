@@ -4,7 +4,7 @@ import torch
 
 import oracle
 
-# Spec tolerances: aprod 1e-12 in the infinity norm scaled by |A||x|
+# Parity tolerances: aprod 1e-12 in the infinity norm scaled by |A||x|
 # (resp. |A|^T|y|); LSQR solutions 1e-9 relative in the 2-norm.
 APROD_TOL = 1e-12
 LSQR_TOL = 1e-9
